@@ -88,6 +88,32 @@ def key_of_rank(seed: int, ranks: np.ndarray) -> np.ndarray:
     return mix(r ^ _U64(key_salt(seed))).view(np.int64)
 
 
+def _unxorshift(y: np.ndarray, s: int) -> np.ndarray:
+    x = y.copy()
+    t = y >> _U64(s)
+    while np.any(t):
+        x ^= t
+        t = t >> _U64(s)
+    return x
+
+
+def unmix(z: np.ndarray) -> np.ndarray:
+    """Inverse of ``mix`` (each xorshift and odd multiply is invertible mod 2**64)."""
+    z = np.asarray(z, dtype=_U64)
+    inv1 = _U64(pow(M1, -1, 1 << 64))
+    inv2 = _U64(pow(M2, -1, 1 << 64))
+    with np.errstate(over="ignore"):
+        z = _unxorshift(z, 31) * inv2
+        z = _unxorshift(z, 27) * inv1
+        return _unxorshift(z, 30)
+
+
+def rank_of_key(seed: int, keys: np.ndarray) -> np.ndarray:
+    """Inverse of ``key_of_rank``: the domain rank of each key (uint64)."""
+    k = np.asarray(keys, dtype=np.int64).view(_U64)
+    return unmix(k) ^ _U64(key_salt(seed))
+
+
 def mulhi_u32(u: np.ndarray, d: int) -> np.ndarray:
     """floor(u * d / 2**64) for uint64 ``u`` and 0 < d < 2**32, exactly."""
     assert 0 < d < (1 << 32)

@@ -1,0 +1,198 @@
+/*
+ * agg.h - C ABI of the GB300 budgeted group-by library (libagg.so).
+ *
+ * The operation (Section 3.1 of Wen, Borkar, Carey and Tsotras, "Revisiting
+ * Aggregation for Data Intensive Applications: A Performance Study"): for every
+ * distinct int64 grouping key among n input rows, one group record holding the
+ * key and its bounded-state aggregates COUNT, SUM, MIN and MAX over the rows
+ * with that key.  AVG is returned as the exact pair (SUM, COUNT).  All
+ * aggregates are integers: COUNT is uint64, SUM is int64 taken modulo 2^64,
+ * MIN and MAX are int64 (int32 input values are widened).
+ *
+ * The work runs under a strictly bounded working-memory budget given at
+ * creation (Section 3.2: "a tightly bounded memory budget to each query").
+ * Groups that do not fit are partitioned, spilled to a staging area and
+ * aggregated recursively, in the hybrid-hash style of Section 4.3 with the
+ * Pre-Partitioning policy of Section 4.3.4 (the table is filled first; once it
+ * is full, rows of resident groups aggregate in place and all other rows are
+ * hash-partitioned and spilled).  A radix-sort + segmented-reduction path
+ * (the Sort-based algorithm of Section 4.1) is available beside it.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are CUDA device pointers (or managed memory); h_* are
+ *    host pointers.  Passing a host pointer where a device pointer is expected
+ *    returns AGG_ERR_INVALID_ARG; there is no CPU fallback.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  agg_run only enqueues work; results are complete in stream
+ *    order, and errors raised on the device are reported by agg_sync.
+ *  - Input and output buffers are owned by the caller.  The library owns its
+ *    working memory (inside the budget) and its staging area (outside it, as
+ *    the paper's M excludes disk: Section 3.2, Section 4.1).
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - Functions return AGG_OK or an agg_status error code; on error, output
+ *    buffer contents are unspecified.
+ */
+#ifndef AGG_H
+#define AGG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum agg_status {
+  AGG_OK = 0,
+  AGG_ERR_INVALID_ARG = 1,       /* NULL/host pointer, bad enum, bad size */
+  AGG_ERR_BUDGET_TOO_SMALL = 2,  /* budget below AGG_MIN_BUDGET */
+  AGG_ERR_OOM = 3,               /* cudaMalloc of working memory or staging failed */
+  AGG_ERR_OUTPUT_CAPACITY = 4,   /* more groups than agg_output.capacity */
+  AGG_ERR_STAGING_EXHAUSTED = 5, /* spill exceeded the reserved staging area */
+  AGG_ERR_TIMEOUT = 6,           /* a bounded device-side wait gave up */
+  AGG_ERR_CUDA = 7,              /* a CUDA runtime call failed */
+  AGG_ERR_INTERNAL = 8           /* invariant violated (for example recursion depth) */
+} agg_status;
+
+/* Aggregate bitmask for agg_spec.ops (Section 3.1 bounded-state functions). */
+enum { AGG_COUNT = 1u, AGG_SUM = 2u, AGG_MIN = 4u, AGG_MAX = 8u };
+
+typedef enum agg_dtype { AGG_I32 = 0, AGG_I64 = 1 } agg_dtype;
+
+/* AGG_PATH_HASH: Pre-Partitioning hybrid hash (Sections 4.3, 4.3.4).
+ * AGG_PATH_SORT: radix sort + segmented reduction (Section 4.1); its output is
+ * in ascending signed key order. */
+typedef enum agg_path { AGG_PATH_HASH = 0, AGG_PATH_SORT = 1 } agg_path;
+
+#define AGG_MIN_BUDGET ((size_t)1 << 20)
+#define AGG_MAX_LEVELS 12
+
+typedef struct agg_spec {
+  uint32_t ops;             /* AGG_COUNT|AGG_SUM|AGG_MIN|AGG_MAX, non-zero */
+  int32_t value_type;       /* agg_dtype of the input values */
+  int32_t path;             /* agg_path */
+  uint32_t flags;           /* reserved, must be 0 */
+  uint64_t expected_groups; /* optional estimate of the result size G (Eq. 1); 0 = unknown */
+  uint64_t seed;            /* hash seed of level 0; each level derives its own (Section 6.7) */
+} agg_spec;
+
+/* Knobs of the hash path; zero fields keep the defaults. */
+typedef struct agg_tuning {
+  double max_load_factor;  /* table fill before it counts as full (default 0.5); the
+                              slot-table-size ratio of Section 6.7 is its inverse */
+  uint32_t smem_entries;   /* per-block shared-memory pre-aggregation entries, power of
+                              two 256..4096 (default 2048); 1 disables the cache */
+  uint32_t fan_out;        /* spill partitions per level, power of two 16..256;
+                              0 = planner (Eq. 1 with fudge factor, Section 4.3) */
+  uint32_t warp_dedup;     /* 0 = default (on), 1 = on, 2 = off */
+  uint32_t reserved;
+  double fudge;            /* fudge factor F of Eq. 1 (default 1.2, Section 6.7) */
+} agg_tuning;
+
+/* Output arrays, device pointers owned by the caller, one row per group.
+ * Arrays of aggregates not in spec.ops may be NULL; keys must not be NULL.
+ * capacity >= n always suffices. d_n_groups (optional) receives the group
+ * count on the device when the run completes. */
+typedef struct agg_output {
+  int64_t* keys;
+  uint64_t* count;
+  int64_t* sum;
+  int64_t* min;
+  int64_t* max;
+  uint64_t capacity;
+  uint64_t* d_n_groups;
+} agg_output;
+
+/* Counters of the last completed run (agg_get_stats). */
+typedef struct agg_stats {
+  uint64_t n_rows;
+  uint64_t n_groups;
+  uint64_t levels;                               /* recursion levels used (1 = no spill) */
+  uint64_t rounds;                               /* table rounds over all levels */
+  uint64_t spill_records[AGG_MAX_LEVELS];        /* records spilled by level L */
+  uint64_t resident_groups[AGG_MAX_LEVELS];      /* groups completed at level L */
+  uint64_t spill_bytes_written;                  /* 16 B per spilled record */
+  uint64_t spill_bytes_read;
+  uint64_t rows_at_full;                         /* level-0 rows seen when the table filled (~R_H) */
+  uint64_t table_slots;
+  uint64_t table_capacity;                       /* groups held before the table counts as full (K) */
+  uint64_t table_bytes;                          /* working memory used inside the budget */
+  uint64_t budget_bytes;
+  uint64_t staging_bytes;                        /* reserved staging (outside the budget) */
+  uint64_t fan_out;
+  uint64_t status_bits;                          /* 1 << agg_status of device-side errors seen */
+} agg_stats;
+
+/* Planner output (host-only arithmetic, no GPU needed). */
+typedef struct agg_plan_info {
+  uint64_t entry_bytes;     /* bytes per table slot entry (32 or 64) */
+  uint64_t table_slots;     /* slots S of the table inside the budget */
+  uint64_t table_capacity;  /* K = floor(max_load_factor * S) */
+  uint64_t fan_out;         /* spill partitions per level */
+  uint64_t active_slots;    /* slots used at level 0 for this n */
+  uint64_t working_bytes;   /* bytes of the budget in use */
+  uint64_t staging_bytes;   /* staging reserved for n rows */
+} agg_plan_info;
+
+typedef struct agg_handle agg_handle;
+
+/* Creates a group-by handle: validates spec, allocates the working memory
+ * (hash table, tags, control block) inside memory_budget_bytes on the current
+ * device and clears it.  Errors: AGG_ERR_INVALID_ARG (NULL out/spec, bad ops,
+ * value_type or path, flags != 0), AGG_ERR_BUDGET_TOO_SMALL, AGG_ERR_OOM,
+ * AGG_ERR_CUDA.  On success *out owns the memory until agg_destroy. */
+agg_status agg_create(size_t memory_budget_bytes, const agg_spec* spec, agg_handle** out);
+
+/* Replaces the tuning knobs (Section 6.7 slot ratio and fudge factor, fan-out,
+ * shared-memory pre-aggregation size, warp dedup).  Results do not depend on
+ * tuning.  Errors: AGG_ERR_INVALID_ARG for out-of-range values. */
+agg_status agg_set_tuning(agg_handle* h, const agg_tuning* t);
+
+/* Reserves the staging area for inputs of up to max_rows rows, so that a later
+ * agg_run with n <= max_rows allocates nothing (and may be captured in a CUDA
+ * graph).  Errors: AGG_ERR_OOM, AGG_ERR_CUDA. */
+agg_status agg_reserve(agg_handle* h, uint64_t max_rows);
+
+/* Enqueues the group-by of n rows on `stream`.  d_keys: n int64 keys; d_vals:
+ * n values of spec.value_type (may be NULL when ops == AGG_COUNT).  Both must
+ * stay valid until the stream reaches the end of the run.  Writes the groups to
+ * `out` in unspecified order (hash path) or ascending key order (sort path) and
+ * the group count to out->d_n_groups.  May call cudaMalloc to grow the staging
+ * area when n exceeds the last reservation (not allowed during stream capture:
+ * AGG_ERR_INVALID_ARG).  Host-side errors are returned; device-side errors
+ * (output capacity, staging exhausted, timeouts) surface in agg_sync. */
+agg_status agg_run(agg_handle* h, const int64_t* d_keys, const void* d_vals, uint64_t n,
+                   const agg_output* out, void* stream);
+
+/* Same group-by on host buffers: copies h_keys/h_vals to device buffers owned
+ * by the handle, runs, waits, and copies the n_groups result rows back into the
+ * host arrays of h_out (capacity counted in rows).  Pinned host memory gives
+ * the full copy bandwidth.  *n_groups receives the group count.  Synchronous. */
+agg_status agg_run_host(agg_handle* h, const int64_t* h_keys, const void* h_vals, uint64_t n,
+                        const agg_output* h_out, uint64_t* n_groups, void* stream);
+
+/* Waits for the last run of h, returns its device-side status and stores the
+ * group count in *n_groups_host (may be NULL).  Clears the device status. */
+agg_status agg_sync(agg_handle* h, uint64_t* n_groups_host);
+
+/* Copies the counters of the last run (waits for it). */
+agg_status agg_get_stats(agg_handle* h, agg_stats* s);
+
+/* Releases every allocation of h (waits for its work first).  NULL is allowed. */
+agg_status agg_destroy(agg_handle* h);
+
+/* Static description of a status code. */
+const char* agg_strerror(agg_status s);
+
+/* Host-only planning: the table size, capacity and fan-out agg_create/agg_run
+ * would choose for this budget, spec and n (Eq. 1 adapted to bytes, Section
+ * 4.3).  No GPU is touched.  Errors: AGG_ERR_INVALID_ARG,
+ * AGG_ERR_BUDGET_TOO_SMALL. */
+agg_status agg_plan(size_t memory_budget_bytes, const agg_spec* spec, const agg_tuning* t, uint64_t n,
+                    agg_plan_info* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AGG_H */

@@ -1,0 +1,117 @@
+"""ctypes declarations of include/agg.h (argument marshalling only).
+
+The shared library is paper_1311_0059_gb300/libagg.so, built in-tree by
+paper_1311_0059_gb300/build.py.  Loading fails loudly when it is missing:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libagg.so")
+ROOT = os.path.dirname(HERE)
+HEADER = os.path.join(ROOT, "include", "agg.h")
+
+AGG_OK = 0
+AGG_ERR_INVALID_ARG = 1
+AGG_ERR_BUDGET_TOO_SMALL = 2
+AGG_ERR_OOM = 3
+AGG_ERR_OUTPUT_CAPACITY = 4
+AGG_ERR_STAGING_EXHAUSTED = 5
+AGG_ERR_TIMEOUT = 6
+AGG_ERR_CUDA = 7
+AGG_ERR_INTERNAL = 8
+
+AGG_COUNT, AGG_SUM, AGG_MIN, AGG_MAX = 1, 2, 4, 8
+AGG_I32, AGG_I64 = 0, 1
+AGG_PATH_HASH, AGG_PATH_SORT = 0, 1
+AGG_MAX_LEVELS = 12
+AGG_MIN_BUDGET = 1 << 20
+
+_P = ctypes.c_void_p
+_U64 = ctypes.c_uint64
+
+
+class agg_spec(ctypes.Structure):
+    _fields_ = [("ops", ctypes.c_uint32), ("value_type", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("expected_groups", ctypes.c_uint64), ("seed", ctypes.c_uint64)]
+
+
+class agg_tuning(ctypes.Structure):
+    _fields_ = [("max_load_factor", ctypes.c_double), ("smem_entries", ctypes.c_uint32),
+                ("fan_out", ctypes.c_uint32), ("warp_dedup", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("fudge", ctypes.c_double)]
+
+
+class agg_output(ctypes.Structure):
+    _fields_ = [("keys", _P), ("count", _P), ("sum", _P), ("min", _P), ("max", _P), ("capacity", ctypes.c_uint64),
+                ("d_n_groups", _P)]
+
+
+class agg_stats(ctypes.Structure):
+    _fields_ = [("n_rows", _U64), ("n_groups", _U64), ("levels", _U64), ("rounds", _U64),
+                ("spill_records", _U64 * AGG_MAX_LEVELS), ("resident_groups", _U64 * AGG_MAX_LEVELS),
+                ("spill_bytes_written", _U64), ("spill_bytes_read", _U64), ("rows_at_full", _U64),
+                ("table_slots", _U64), ("table_capacity", _U64), ("table_bytes", _U64), ("budget_bytes", _U64),
+                ("staging_bytes", _U64), ("fan_out", _U64), ("status_bits", _U64)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["spill_records"] = list(self.spill_records)
+        d["resident_groups"] = list(self.resident_groups)
+        return d
+
+
+class agg_plan_info(ctypes.Structure):
+    _fields_ = [("entry_bytes", _U64), ("table_slots", _U64), ("table_capacity", _U64), ("fan_out", _U64),
+                ("active_slots", _U64), ("working_bytes", _U64), ("staging_bytes", _U64)]
+
+
+# name -> (restype, argtypes); the names are exactly those declared in include/agg.h
+SIGNATURES = {
+    "agg_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(agg_spec), ctypes.POINTER(_P)]),
+    "agg_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(agg_tuning)]),
+    "agg_reserve": (ctypes.c_int, [_P, _U64]),
+    "agg_run": (ctypes.c_int, [_P, _P, _P, _U64, ctypes.POINTER(agg_output), _P]),
+    "agg_run_host": (ctypes.c_int, [_P, _P, _P, _U64, ctypes.POINTER(agg_output), ctypes.POINTER(_U64), _P]),
+    "agg_sync": (ctypes.c_int, [_P, ctypes.POINTER(_U64)]),
+    "agg_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(agg_stats)]),
+    "agg_destroy": (ctypes.c_int, [_P]),
+    "agg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "agg_plan": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(agg_spec), ctypes.POINTER(agg_tuning), _U64,
+                                ctypes.POINTER(agg_plan_info)]),
+}
+
+_LIB = None
+
+
+class AggError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+def load(path: str = LIB_PATH):
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_1311_0059_gb300/build.py "
+                               "(the group-by has no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def strerror(status: int) -> str:
+    return load().agg_strerror(int(status)).decode()
+
+
+def check(status: int, where: str):
+    if status != AGG_OK:
+        raise AggError(status, where)

@@ -1,0 +1,586 @@
+// C ABI of libagg.so: handle lifetime, planning, staging reservation, runs.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "agg_internal.cuh"
+#include "sort_path.cuh"
+
+using namespace agg;
+
+struct agg_handle {
+  int device = 0;
+  size_t budget = 0;
+  agg_spec spec{};
+  agg_tuning tune{};
+  int ent_kind = 0;
+  uint32_t es = 32;
+  uint64_t slots = 0;
+  uint64_t working_bytes = 0;
+  // working memory (inside the budget)
+  void* work = nullptr;
+  Ctrl* ctrl = nullptr;
+  uint32_t* tags = nullptr;
+  uint8_t* ent = nullptr;
+  KernelInfo ki{};
+  // staging (outside the budget)
+  void* stg_mem[2] = {nullptr, nullptr};
+  uint8_t* stg[2] = {nullptr, nullptr};
+  uint32_t* dir_part[2] = {nullptr, nullptr};
+  uint32_t* dir_count[2] = {nullptr, nullptr};
+  uint32_t* list[2] = {nullptr, nullptr};
+  uint64_t max_chunks = 0;
+  uint64_t reserved_rows = 0;
+  uint32_t reserved_fan = 0;
+  uint64_t staging_bytes = 0;
+  // device copies for agg_run_host
+  void* in_buf = nullptr;
+  uint64_t in_cap = 0;
+  void* out_buf = nullptr;
+  uint64_t out_cap = 0;
+  uint64_t* ng_host = nullptr;  // pinned
+  // sort path working state
+  SortState sort{};
+  cudaStream_t last_stream = nullptr;
+  bool ran = false;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+constexpr double DEFAULT_LF = 0.5;
+constexpr uint32_t DEFAULT_NS = 2048;
+constexpr double DEFAULT_FUDGE = 1.2;
+constexpr uint64_t TIMEOUT_NS = 4000000000ull;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool valid_spec(const agg_spec* s) {
+  if (!s) return false;
+  if (s->ops == 0 || (s->ops & ~15u)) return false;
+  if (s->value_type != AGG_I32 && s->value_type != AGG_I64) return false;
+  if (s->path != AGG_PATH_HASH && s->path != AGG_PATH_SORT) return false;
+  if (s->flags != 0) return false;
+  return true;
+}
+
+int pick_ent(const agg_spec* s) {
+  if ((s->ops & (AGG_MIN | AGG_MAX)) == 0) return ENT32_CS;
+  return s->value_type == AGG_I32 ? ENT32_CSMM32 : ENT64;
+}
+
+agg_tuning effective(const agg_tuning* t) {
+  agg_tuning e{};
+  e.max_load_factor = (t && t->max_load_factor > 0) ? t->max_load_factor : DEFAULT_LF;
+  e.smem_entries = (t && t->smem_entries) ? t->smem_entries : DEFAULT_NS;
+  e.fan_out = t ? t->fan_out : 0;
+  e.warp_dedup = (t && t->warp_dedup) ? t->warp_dedup : 1;
+  e.fudge = (t && t->fudge > 0) ? t->fudge : DEFAULT_FUDGE;
+  return e;
+}
+
+bool valid_tuning(const agg_tuning* t) {
+  if (!t) return true;
+  if (t->max_load_factor < 0 || t->max_load_factor > 0.95) return false;
+  if (t->smem_entries > 1) {
+    if (t->smem_entries < 256 || t->smem_entries > 4096 || (t->smem_entries & (t->smem_entries - 1))) return false;
+  }
+  if (t->fan_out && (t->fan_out < 16 || t->fan_out > 256 || (t->fan_out & (t->fan_out - 1)))) return false;
+  if (t->warp_dedup > 2) return false;
+  if (t->fudge < 0 || t->fudge > 16) return false;
+  return true;
+}
+
+uint32_t next_pow2(uint64_t x) {
+  uint32_t p = 1;
+  while (p < x && p < (1u << 30)) p <<= 1;
+  return p;
+}
+
+// Fan-out of the spill partitioning.  Eq. 1 (Section 4.3) gives the spilled
+// partitions P = (G*F - M)/(M - 2) for a budget of M frames; with a frame-free
+// byte budget M >> 2 this is P ~ G*F/M - 1 (G and M in bytes), the count that
+// lets every spilled partition be aggregated within the budget next level.
+// G is the result size: expected_groups if given, else n (an upper bound).
+uint32_t plan_fan(const agg_spec* s, const agg_tuning& t, uint64_t n, size_t budget, uint32_t es) {
+  if (t.fan_out) return t.fan_out;
+  const double g = (double)(s->expected_groups ? s->expected_groups : n);
+  const double p = g * (double)es * t.fudge / (double)budget;
+  uint64_t want = (uint64_t)std::ceil(p > 1 ? p : 1);
+  uint32_t f = next_pow2(want);
+  if (f < 16) f = 16;
+  if (f > 256) f = 256;
+  return f;
+}
+
+uint32_t log2u(uint32_t x) {
+  uint32_t l = 0;
+  while ((1u << l) < x) ++l;
+  return l;
+}
+
+struct Layout {
+  uint64_t ctrl_bytes, tags_off, ent_off, slots, total;
+};
+
+bool layout_for(size_t budget, uint32_t es, Layout* L) {
+  L->ctrl_bytes = align_up(sizeof(Ctrl), 256);
+  if (budget < AGG_MIN_BUDGET) return false;
+  uint64_t avail = budget - L->ctrl_bytes - 512;
+  uint64_t s = (avail / (es + 1)) & ~3ull;
+  if (s > (1ull << 31) - 4) s = (1ull << 31) - 4;
+  L->slots = s;
+  L->tags_off = L->ctrl_bytes;
+  L->ent_off = align_up(L->tags_off + s, 256);
+  L->total = L->ent_off + s * es;
+  return s >= MIN_SLOTS && L->total <= budget;
+}
+
+uint32_t active_slots(uint64_t est, double lf, uint64_t slots) {
+  uint64_t want = (uint64_t)((double)est / lf) + 4;
+  want = (want + 3) & ~3ull;
+  if (want < MIN_SLOTS) want = MIN_SLOTS;
+  if (want > slots) want = slots;
+  return (uint32_t)want;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void free_staging(agg_handle* h) {
+  for (int a = 0; a < 2; ++a) {
+    if (h->stg_mem[a]) cudaFree(h->stg_mem[a]);
+    h->stg_mem[a] = nullptr;
+    h->stg[a] = nullptr;
+    h->dir_part[a] = h->dir_count[a] = h->list[a] = nullptr;
+  }
+  h->max_chunks = 0;
+  h->reserved_rows = 0;
+  h->reserved_fan = 0;
+  h->staging_bytes = 0;
+}
+
+agg_status reserve_staging(agg_handle* h, uint64_t rows, uint32_t fan) {
+  if (h->stg_mem[0] && rows <= h->reserved_rows && fan <= h->reserved_fan) return AGG_OK;
+  if (rows < h->reserved_rows) rows = h->reserved_rows;
+  if (fan < h->reserved_fan) fan = h->reserved_fan;
+  free_staging(h);
+  const uint64_t chunks = (rows + CH - 1) / CH + (uint64_t)h->ki.blocks * fan + 8;
+  const uint64_t data = align_up(chunks * CH * REC_BYTES, 256);
+  const uint64_t meta = align_up(chunks * 4, 256);
+  const uint64_t per_area = data + 3 * meta;
+  for (int a = 0; a < 2; ++a) {
+    void* m = nullptr;
+    if (cudaMalloc(&m, per_area) != cudaSuccess) {
+      cudaGetLastError();
+      free_staging(h);
+      return AGG_ERR_OOM;
+    }
+    h->stg_mem[a] = m;
+    uint8_t* b = static_cast<uint8_t*>(m);
+    h->stg[a] = b;
+    h->dir_part[a] = reinterpret_cast<uint32_t*>(b + data);
+    h->dir_count[a] = reinterpret_cast<uint32_t*>(b + data + meta);
+    h->list[a] = reinterpret_cast<uint32_t*>(b + data + 2 * meta);
+  }
+  h->max_chunks = chunks;
+  h->reserved_rows = rows;
+  h->reserved_fan = fan;
+  h->staging_bytes = 2 * per_area;
+  return AGG_OK;
+}
+
+agg_status reinit_working(agg_handle* h, cudaStream_t s) {
+  if (cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return AGG_ERR_CUDA;
+  const unsigned long long none = ~0ull;
+  if (cudaMemcpyAsync(&h->ctrl->rows_at_full, &none, 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return AGG_ERR_CUDA;
+  if (hash_init_table(h->ent, h->tags, (uint32_t)h->slots, h->ent_kind, s) != cudaSuccess) return AGG_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return AGG_ERR_CUDA;
+  return AGG_OK;
+}
+
+agg_status status_from_bits(unsigned long long bits) {
+  const agg_status order[] = {AGG_ERR_TIMEOUT, AGG_ERR_INTERNAL, AGG_ERR_STAGING_EXHAUSTED, AGG_ERR_OUTPUT_CAPACITY};
+  for (agg_status s : order)
+    if (bits & (1ull << (int)s)) return s;
+  return bits ? AGG_ERR_INTERNAL : AGG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* agg_strerror(agg_status s) {
+  switch (s) {
+    case AGG_OK: return "ok";
+    case AGG_ERR_INVALID_ARG: return "invalid argument";
+    case AGG_ERR_BUDGET_TOO_SMALL: return "memory budget too small";
+    case AGG_ERR_OOM: return "device memory allocation failed";
+    case AGG_ERR_OUTPUT_CAPACITY: return "output capacity too small for the number of groups";
+    case AGG_ERR_STAGING_EXHAUSTED: return "spill exceeded the reserved staging area";
+    case AGG_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+    case AGG_ERR_CUDA: return "CUDA runtime error";
+    case AGG_ERR_INTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+agg_status agg_plan(size_t budget, const agg_spec* spec, const agg_tuning* t, uint64_t n, agg_plan_info* out) {
+  if (!valid_spec(spec) || !out || !valid_tuning(t)) return AGG_ERR_INVALID_ARG;
+  if (budget < AGG_MIN_BUDGET) return AGG_ERR_BUDGET_TOO_SMALL;
+  const agg_tuning e = effective(t);
+  const uint32_t es = entry_bytes(pick_ent(spec));
+  Layout L;
+  if (!layout_for(budget, es, &L)) return AGG_ERR_BUDGET_TOO_SMALL;
+  out->entry_bytes = es;
+  out->table_slots = L.slots;
+  out->table_capacity = (uint64_t)(e.max_load_factor * (double)L.slots);
+  out->fan_out = plan_fan(spec, e, n, budget, es);
+  out->active_slots = active_slots(spec->expected_groups ? spec->expected_groups : (n ? n : 1),
+                                   e.max_load_factor, L.slots);
+  out->working_bytes = L.total;
+  const uint64_t chunks = (n + CH - 1) / CH + 152ull * 2 * out->fan_out + 8;
+  out->staging_bytes = 2 * (chunks * CH * REC_BYTES + 3 * chunks * 4);
+  return AGG_OK;
+}
+
+agg_status agg_create(size_t budget, const agg_spec* spec, agg_handle** out) {
+  if (!out || !valid_spec(spec)) return AGG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (budget < AGG_MIN_BUDGET) return AGG_ERR_BUDGET_TOO_SMALL;
+  agg_handle* h = new (std::nothrow) agg_handle();
+  if (!h) return AGG_ERR_OOM;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return AGG_ERR_CUDA;
+  }
+  h->budget = budget;
+  h->spec = *spec;
+  h->tune = effective(nullptr);
+  h->ent_kind = pick_ent(spec);
+  h->es = entry_bytes(h->ent_kind);
+  Layout L;
+  if (!layout_for(budget, h->es, &L)) {
+    delete h;
+    return AGG_ERR_BUDGET_TOO_SMALL;
+  }
+  h->slots = L.slots;
+  h->working_bytes = L.total;
+  if (cudaMalloc(&h->work, L.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return AGG_ERR_OOM;
+  }
+  uint8_t* b = static_cast<uint8_t*>(h->work);
+  h->ctrl = reinterpret_cast<Ctrl*>(b);
+  h->tags = reinterpret_cast<uint32_t*>(b + L.tags_off);
+  h->ent = b + L.ent_off;
+  if (cudaMallocHost(&h->ng_host, 64) != cudaSuccess) {
+    cudaGetLastError();
+    agg_destroy(h);
+    return AGG_ERR_OOM;
+  }
+  if (hash_kernel_info(h->ent_kind, spec->value_type, h->tune.smem_entries > 1 ? h->tune.smem_entries : 0,
+                       h->device, &h->ki) != cudaSuccess) {
+    cudaGetLastError();
+    agg_destroy(h);
+    return AGG_ERR_CUDA;
+  }
+  agg_status st = reinit_working(h, nullptr);
+  if (st != AGG_OK) {
+    agg_destroy(h);
+    return st;
+  }
+  *out = h;
+  return AGG_OK;
+}
+
+agg_status agg_set_tuning(agg_handle* h, const agg_tuning* t) {
+  if (!h || !valid_tuning(t)) return AGG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  const agg_tuning e = effective(t);
+  KernelInfo ki;
+  if (hash_kernel_info(h->ent_kind, h->spec.value_type, e.smem_entries > 1 ? e.smem_entries : 0, h->device, &ki) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return AGG_ERR_CUDA;
+  }
+  if (ki.blocks > h->ki.blocks && h->stg_mem[0]) {
+    // more blocks means more open chunks: re-reserve on the next run
+    const uint64_t rows = h->reserved_rows;
+    const uint32_t fan = h->reserved_fan;
+    cudaDeviceSynchronize();
+    free_staging(h);
+    h->ki = ki;
+    h->tune = e;
+    return reserve_staging(h, rows, fan);
+  }
+  h->ki = ki;
+  h->tune = e;
+  return AGG_OK;
+}
+
+agg_status agg_reserve(agg_handle* h, uint64_t max_rows) {
+  if (!h) return AGG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  const uint32_t fan = plan_fan(&h->spec, h->tune, max_rows, h->budget, h->es);
+  if (h->spec.path == AGG_PATH_SORT) {
+    agg_status st = sort_reserve(h->sort, max_rows, h->budget, h->spec);
+    if (st != AGG_OK) return st;
+  }
+  return reserve_staging(h, max_rows, fan);
+}
+
+agg_status agg_run(agg_handle* h, const int64_t* d_keys, const void* d_vals, uint64_t n, const agg_output* out,
+                   void* stream) {
+  if (!h || !out) return AGG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool need_vals = (h->spec.ops & ~(uint32_t)AGG_COUNT) != 0;
+  if (n > 0) {
+    if (!is_device_ptr(d_keys)) return AGG_ERR_INVALID_ARG;
+    if (need_vals && !is_device_ptr(d_vals)) return AGG_ERR_INVALID_ARG;
+    if (d_vals && !is_device_ptr(d_vals)) return AGG_ERR_INVALID_ARG;
+  }
+  if (!out->keys || !is_device_ptr(out->keys)) return AGG_ERR_INVALID_ARG;
+  if ((h->spec.ops & AGG_COUNT) && !is_device_ptr(out->count)) return AGG_ERR_INVALID_ARG;
+  if ((h->spec.ops & AGG_SUM) && !is_device_ptr(out->sum)) return AGG_ERR_INVALID_ARG;
+  if ((h->spec.ops & AGG_MIN) && !is_device_ptr(out->min)) return AGG_ERR_INVALID_ARG;
+  if ((h->spec.ops & AGG_MAX) && !is_device_ptr(out->max)) return AGG_ERR_INVALID_ARG;
+  if (out->d_n_groups && !is_device_ptr(out->d_n_groups)) return AGG_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_keys) & 7) ||
+      (d_vals && (reinterpret_cast<uintptr_t>(d_vals) & (h->spec.value_type == AGG_I64 ? 7 : 3))))
+    return AGG_ERR_INVALID_ARG;
+
+  if (h->spec.path == AGG_PATH_SORT) {
+    agg_status st = sort_run(h->sort, h->budget, h->spec, h->ctrl, d_keys, d_vals, n, out, s);
+    h->last_stream = s;
+    h->ran = true;
+    return st;
+  }
+
+  const uint32_t fan = plan_fan(&h->spec, h->tune, n, h->budget, h->es);
+  if (!h->stg_mem[0] || n > h->reserved_rows || fan > h->reserved_fan) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      return AGG_ERR_INVALID_ARG;  // staging must be reserved before capture
+    cudaGetLastError();
+    agg_status st = reserve_staging(h, n, fan);
+    if (st != AGG_OK) return st;
+  }
+
+  HashParams p{};
+  p.keys = d_keys;
+  p.vals = d_vals;
+  p.n = n;
+  p.has_vals = d_vals != nullptr;
+  p.vec_ok = ((reinterpret_cast<uintptr_t>(d_keys) & 15) == 0) &&
+             (!d_vals || (reinterpret_cast<uintptr_t>(d_vals) & (h->spec.value_type == AGG_I64 ? 15 : 7)) == 0);
+  p.o_keys = out->keys;
+  p.o_count = (h->spec.ops & AGG_COUNT) ? out->count : nullptr;
+  p.o_sum = (h->spec.ops & AGG_SUM) ? out->sum : nullptr;
+  p.o_min = (h->spec.ops & AGG_MIN) ? out->min : nullptr;
+  p.o_max = (h->spec.ops & AGG_MAX) ? out->max : nullptr;
+  p.o_cap = out->capacity;
+  p.o_ngroups = out->d_n_groups;
+  p.ctrl = h->ctrl;
+  p.ent = h->ent;
+  p.tags = h->tags;
+  p.slots = (uint32_t)h->slots;
+  for (int a = 0; a < 2; ++a) {
+    p.stg[a] = h->stg[a];
+    p.dir_part[a] = h->dir_part[a];
+    p.dir_count[a] = h->dir_count[a];
+    p.list[a] = h->list[a];
+    p.max_chunks[a] = h->max_chunks;
+  }
+  p.seed = h->spec.seed;
+  p.ops = h->spec.ops;
+  p.fan_log2 = log2u(fan);
+  p.lf = h->tune.max_load_factor;
+  p.s_act0 = active_slots(h->spec.expected_groups ? h->spec.expected_groups : (n ? n : 1), p.lf, h->slots);
+  p.ns = h->tune.smem_entries > 1 ? h->tune.smem_entries : 0;
+  p.dedup = h->tune.warp_dedup == 1 ? 1 : 0;
+  p.timeout_ns = TIMEOUT_NS;
+  if (hash_launch(h->ent_kind, h->spec.value_type, p, h->ki, s) != cudaSuccess) {
+    cudaGetLastError();
+    return AGG_ERR_CUDA;
+  }
+  h->last_stream = s;
+  h->ran = true;
+  return AGG_OK;
+}
+
+agg_status agg_sync(agg_handle* h, uint64_t* n_groups_host) {
+  if (!h) return AGG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) {
+    cudaGetLastError();
+    return AGG_ERR_CUDA;
+  }
+  unsigned long long bits = 0, ng = 0;
+  if (cudaMemcpy(&bits, &h->ctrl->status_bits, 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&ng, &h->ctrl->last_n_groups, 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return AGG_ERR_CUDA;
+  }
+  if (n_groups_host) *n_groups_host = ng;
+  const agg_status st = status_from_bits(bits);
+  if (bits) {
+    if (bits & (1ull << (int)AGG_ERR_TIMEOUT)) {
+      // a timed-out wait leaves barrier state behind: rebuild the working memory
+      cudaDeviceSynchronize();
+      agg_status r = reinit_working(h, nullptr);
+      if (r != AGG_OK) return r;
+    } else {
+      unsigned long long zero = 0;
+      cudaMemcpy(&h->ctrl->status_bits, &zero, 8, cudaMemcpyHostToDevice);
+    }
+  }
+  return st;
+}
+
+agg_status agg_get_stats(agg_handle* h, agg_stats* s) {
+  if (!h || !s) return AGG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) {
+    cudaGetLastError();
+    return AGG_ERR_CUDA;
+  }
+  Ctrl c;
+  if (cudaMemcpy(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return AGG_ERR_CUDA;
+  }
+  std::memset(s, 0, sizeof(*s));
+  s->n_rows = c.last_n_rows;
+  s->n_groups = c.last_n_groups;
+  s->levels = c.last_levels;
+  s->rounds = c.last_rounds;
+  uint64_t spilled = 0;
+  for (int l = 0; l < AGG_MAX_LEVELS; ++l) {
+    s->spill_records[l] = c.last_spill_records[l];
+    s->resident_groups[l] = c.last_resident_groups[l];
+    spilled += c.last_spill_records[l];
+  }
+  s->spill_bytes_written = spilled * REC_BYTES;
+  s->spill_bytes_read = spilled * REC_BYTES;
+  s->rows_at_full = c.last_rows_at_full;
+  s->table_slots = h->slots;
+  s->table_capacity = (uint64_t)(h->tune.max_load_factor * (double)h->slots);
+  s->table_bytes = h->working_bytes;
+  s->budget_bytes = h->budget;
+  s->staging_bytes = h->staging_bytes + sort_staging_bytes(h->sort);
+  s->fan_out = plan_fan(&h->spec, h->tune, c.last_n_rows, h->budget, h->es);
+  s->status_bits = c.status_bits;
+  if (h->spec.path == AGG_PATH_SORT) sort_fill_stats(h->sort, s);
+  return AGG_OK;
+}
+
+agg_status agg_run_host(agg_handle* h, const int64_t* h_keys, const void* h_vals, uint64_t n, const agg_output* h_out,
+                        uint64_t* n_groups, void* stream) {
+  if (!h || !h_out || !h_out->keys || (n > 0 && !h_keys)) return AGG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t vb = h->spec.value_type == AGG_I64 ? 8 : 4;
+  const uint64_t rows = n ? n : 1;
+  if (rows > h->in_cap) {
+    if (h->in_buf) cudaFree(h->in_buf);
+    h->in_buf = nullptr;
+    h->in_cap = 0;
+    if (cudaMalloc(&h->in_buf, rows * (8 + 8)) != cudaSuccess) {
+      cudaGetLastError();
+      return AGG_ERR_OOM;
+    }
+    h->in_cap = rows;
+  }
+  if (rows > h->out_cap) {
+    if (h->out_buf) cudaFree(h->out_buf);
+    h->out_buf = nullptr;
+    h->out_cap = 0;
+    if (cudaMalloc(&h->out_buf, rows * 40 + 64) != cudaSuccess) {
+      cudaGetLastError();
+      return AGG_ERR_OOM;
+    }
+    h->out_cap = rows;
+  }
+  int64_t* dk = static_cast<int64_t*>(h->in_buf);
+  void* dv = h_vals ? static_cast<void*>(static_cast<uint8_t*>(h->in_buf) + rows * 8) : nullptr;
+  uint8_t* ob = static_cast<uint8_t*>(h->out_buf);
+  agg_output dout{};
+  dout.keys = reinterpret_cast<int64_t*>(ob);
+  dout.count = reinterpret_cast<uint64_t*>(ob + rows * 8);
+  dout.sum = reinterpret_cast<int64_t*>(ob + rows * 16);
+  dout.min = reinterpret_cast<int64_t*>(ob + rows * 24);
+  dout.max = reinterpret_cast<int64_t*>(ob + rows * 32);
+  dout.capacity = rows;
+  dout.d_n_groups = reinterpret_cast<uint64_t*>(ob + rows * 40);
+  if (n > 0) {
+    if (cudaMemcpyAsync(dk, h_keys, n * 8, cudaMemcpyDefault, s) != cudaSuccess) return AGG_ERR_CUDA;
+    if (dv && cudaMemcpyAsync(dv, h_vals, n * vb, cudaMemcpyDefault, s) != cudaSuccess) return AGG_ERR_CUDA;
+  }
+  agg_status st = agg_run(h, dk, dv, n, &dout, stream);
+  if (st != AGG_OK) return st;
+  if (cudaMemcpyAsync(h->ng_host, dout.d_n_groups, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return AGG_ERR_CUDA;
+  uint64_t ng = 0;
+  st = agg_sync(h, &ng);
+  if (st != AGG_OK) return st;
+  ng = h->ng_host[0];
+  if (n_groups) *n_groups = ng;
+  if (ng > h_out->capacity) return AGG_ERR_OUTPUT_CAPACITY;
+  if (ng > 0) {
+    struct {
+      void* dst;
+      const void* src;
+      bool want;
+    } cp[5] = {{h_out->keys, dout.keys, true},
+               {h_out->count, dout.count, (h->spec.ops & AGG_COUNT) != 0},
+               {h_out->sum, dout.sum, (h->spec.ops & AGG_SUM) != 0},
+               {h_out->min, dout.min, (h->spec.ops & AGG_MIN) != 0},
+               {h_out->max, dout.max, (h->spec.ops & AGG_MAX) != 0}};
+    for (auto& c : cp)
+      if (c.want && c.dst && cudaMemcpyAsync(c.dst, c.src, ng * 8, cudaMemcpyDefault, s) != cudaSuccess)
+        return AGG_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return AGG_ERR_CUDA;
+  return AGG_OK;
+}
+
+agg_status agg_destroy(agg_handle* h) {
+  if (!h) return AGG_OK;
+  DeviceGuard g(h->device);
+  cudaDeviceSynchronize();
+  cudaGetLastError();
+  free_staging(h);
+  sort_free(h->sort);
+  if (h->work) cudaFree(h->work);
+  if (h->in_buf) cudaFree(h->in_buf);
+  if (h->out_buf) cudaFree(h->out_buf);
+  if (h->ng_host) cudaFreeHost(h->ng_host);
+  delete h;
+  return AGG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Internal definitions shared by the CUDA translation units of libagg.so.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "agg.h"
+
+namespace agg {
+
+// ---------------------------------------------------------------- geometry
+constexpr int THREADS = 512;               // threads per block of the hash kernel
+constexpr int RPT = 4;                     // rows per thread per tile
+constexpr int TILE = THREADS * RPT;        // rows per block tile
+constexpr uint32_t CH = 2048;              // records per staging chunk (32 KiB)
+constexpr int MAX_FAN = 256;               // largest spill fan-out
+constexpr int MAX_PROBE = 128;             // slots examined before a key counts as absent
+constexpr uint32_t MIN_SLOTS = 4096;       // smallest active table of a round
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr uint32_t TAG_EMPTY = 0x00, TAG_CLOSED = 0x01, TAG_BUSY = 0x02;  // occupied: 0x80 | 7 hash bits
+constexpr int64_t SKEY_EMPTY = INT64_MIN;  // empty marker of the shared-memory cache
+constexpr uint64_t REC_BYTES = 16;         // spilled record: (int64 key, int64 value)
+// One tile adds at most TILE rows to a partition, so at most one new chunk is
+// opened per partition per tile.
+static_assert(TILE <= (int)CH, "a tile must fit in one staging chunk");
+
+// Table entry layouts (bytes): key, count, sum, then MIN/MAX when requested.
+enum EntKind { ENT32_CS = 0, ENT32_CSMM32 = 1, ENT64 = 2 };
+inline __host__ __device__ uint32_t entry_bytes(int kind) { return kind == ENT64 ? 64u : 32u; }
+
+// Control block at the start of the working memory (inside the budget).
+// Fields under "run" are zeroed by the last block of every run; the barrier
+// words persist.
+struct alignas(128) Ctrl {
+  unsigned int bar_count;
+  unsigned int pad0[31];
+  unsigned int bar_gen;
+  unsigned int pad1[31];
+  unsigned int done_count;
+  unsigned int pad2[31];
+  // ---- run
+  unsigned long long status_bits;  // 1 << agg_status (cleared by agg_sync)
+  unsigned long long occupancy;    // slots claimed in the current round
+  unsigned long long out_count;    // groups written so far
+  unsigned long long pool_next[2]; // chunks handed out per staging area
+  unsigned long long rows_at_full; // level-0 row index when the table became full
+  unsigned long long rounds;
+  unsigned long long spill_records[AGG_MAX_LEVELS];
+  unsigned long long resident_groups[AGG_MAX_LEVELS];
+  unsigned long long part_records[2][MAX_FAN];
+  unsigned int part_chunks[2][MAX_FAN];
+  unsigned int part_cursor[2][MAX_FAN];
+  // ---- snapshot of the last completed run
+  unsigned long long last_n_rows;
+  unsigned long long last_n_groups;
+  unsigned long long last_levels;
+  unsigned long long last_rounds;
+  unsigned long long last_rows_at_full;
+  unsigned long long last_spill_records[AGG_MAX_LEVELS];
+  unsigned long long last_resident_groups[AGG_MAX_LEVELS];
+};
+
+// Everything one hash-path kernel launch needs (passed by value).
+struct HashParams {
+  const int64_t* keys;
+  const void* vals;
+  uint64_t n;
+  int vec_ok;          // keys/vals aligned for vector loads
+  int has_vals;
+  int64_t* o_keys;
+  uint64_t* o_count;
+  int64_t* o_sum;
+  int64_t* o_min;
+  int64_t* o_max;
+  uint64_t o_cap;
+  uint64_t* o_ngroups;
+  Ctrl* ctrl;
+  uint8_t* ent;
+  uint32_t* tags;
+  uint32_t slots;      // physical slots S (multiple of 4)
+  uint8_t* stg[2];     // staging areas (chunks of CH records)
+  uint32_t* dir_part[2];
+  uint32_t* dir_count[2];
+  uint32_t* list[2];
+  uint64_t max_chunks[2];
+  uint64_t seed;
+  uint32_t ops;
+  uint32_t fan_log2;
+  double lf;           // maximum load factor
+  uint32_t s_act0;     // active slots at level 0
+  uint32_t ns;         // shared-memory cache entries (power of two) or 0
+  uint32_t dedup;      // warp-level key dedup on/off
+  uint32_t pad;
+  uint64_t timeout_ns; // bounded waits give up after this long
+};
+
+struct KernelInfo {
+  int blocks;          // cooperative grid size
+  size_t smem;         // dynamic shared memory per block
+};
+
+// hash_path.cu
+cudaError_t hash_kernel_info(int ent_kind, int vt, uint32_t ns, int device, KernelInfo* out);
+cudaError_t hash_launch(int ent_kind, int vt, const HashParams& p, const KernelInfo& ki, cudaStream_t s);
+cudaError_t hash_init_table(uint8_t* ent, uint32_t* tags, uint32_t slots, int ent_kind, cudaStream_t s);
+
+}  // namespace agg

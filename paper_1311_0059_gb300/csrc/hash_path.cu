@@ -1,0 +1,936 @@
+// Hash path of the budgeted group-by: one persistent cooperative kernel per run.
+//
+// Level 0 streams the input once (Section 4.3, Phase 1).  Each row's key is
+// hashed with the MurmurHash3 64-bit finaliser under a per-level seed (Section
+// 6.7).  Duplicates inside a warp are combined first (match_any + shuffles),
+// then a per-block shared-memory cache of resident groups absorbs hot keys, and
+// the remaining updates go to the global open-addressing table with 64-bit
+// atomics.  The table follows the Pre-Partitioning policy (Section 4.3.4): new
+// groups are inserted until the table is full; afterwards a key that is not
+// resident is spilled, so every group is either completed in place or spilled
+// whole.  Spilled rows are radix-partitioned on hash bits into staging chunks
+// (the run files of Section 4.3) with warp-aggregated cursors.  After the pass
+// the table is emitted and reset.  Spilled partitions are then processed level
+// by level (Phase 2) with fresh seeds; small partitions are packed into one
+// table round (partition tuning, Section 4.3.3).  Phases are separated by grid
+// barriers whose waits are bounded.
+//
+// Residency protocol.  One tag byte per slot is the synchronisation point:
+// EMPTY, CLOSED, BUSY or 0x80|7 hash bits.  An insert CASes EMPTY->BUSY on the
+// tag word, writes the key, fences, and turns BUSY into its tag.  Once the
+// table is full a lookup that reaches an EMPTY slot CASes it to CLOSED instead,
+// which ends that probe chain for good.  Exactly one of "insert k" and "close
+// k's chain" wins the CAS, so a key can never be both resident and spilled.
+#include <cstdio>
+
+#include "agg_internal.cuh"
+
+namespace agg {
+namespace {
+
+constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
+constexpr int WARPS = THREADS / 32;
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+// Seed of recursion level L: a fresh, uncorrelated hash function per level.
+__device__ __forceinline__ uint64_t level_seed(uint64_t seed, uint32_t level) {
+  return fmix64(seed + 0xD6E8FEB86659FD93ull * (uint64_t)(level + 1));
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ void set_status(Ctrl* c, agg_status s) {
+  atomicOr(&c->status_bits, 1ull << (int)s);
+}
+
+// ---------------------------------------------------------------- shared memory
+
+struct Smem {
+  uint32_t cnt[MAX_FAN];   // spill: rows of this tile per partition; P1: chunk histogram
+  uint32_t cur[MAX_FAN];   // current staging chunk per partition (NONE = none)
+  uint32_t fill[MAX_FAN];  // records in the current chunk (CH when none)
+  uint32_t nxt[MAX_FAN];   // chunk opened for this tile's overflow
+  uint32_t begin[MAX_FAN + 1];
+  unsigned long long hrec[MAX_FAN];
+  unsigned long long spilled;
+  unsigned long long scan_base;
+  uint32_t warp_tot[WARPS];
+  uint32_t scan_total;
+  uint32_t claims;
+  uint32_t full;
+  uint32_t ok;
+  uint32_t cache_used;
+};
+
+struct Cache {
+  long long* key;
+  unsigned long long* cnt;
+  unsigned long long* sum;
+  long long* mn;
+  long long* mx;
+  uint32_t* slot;
+  uint32_t n;  // 0 = disabled
+};
+
+__host__ __device__ inline size_t cache_bytes(uint32_t ns, bool mm) {
+  return (size_t)ns * (8 + 8 + 8 + 4 + (mm ? 16 : 0));
+}
+
+__device__ inline Cache carve_cache(unsigned char* base, uint32_t ns, bool mm) {
+  Cache c;
+  c.n = ns;
+  unsigned char* p = base;
+  c.key = reinterpret_cast<long long*>(p);
+  p += (size_t)ns * 8;
+  c.cnt = reinterpret_cast<unsigned long long*>(p);
+  p += (size_t)ns * 8;
+  c.sum = reinterpret_cast<unsigned long long*>(p);
+  p += (size_t)ns * 8;
+  if (mm) {
+    c.mn = reinterpret_cast<long long*>(p);
+    p += (size_t)ns * 8;
+    c.mx = reinterpret_cast<long long*>(p);
+    p += (size_t)ns * 8;
+  } else {
+    c.mn = c.mx = nullptr;
+  }
+  c.slot = reinterpret_cast<uint32_t*>(p);
+  return c;
+}
+
+// ---------------------------------------------------------------- grid barrier
+
+// Sense-counting grid barrier for a cooperative launch.  The wait is bounded:
+// after timeout_ns the block records AGG_ERR_TIMEOUT and returns false.
+__device__ bool grid_barrier(Ctrl* c, uint64_t timeout_ns, Smem& S) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t ok = 1;
+    const uint32_t g = ld_acquire_u32(&c->bar_gen);
+    __threadfence();
+    const uint32_t arrived = atomicAdd(&c->bar_count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&c->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    } else {
+      const uint64_t t0 = globaltimer();
+      while (ld_acquire_u32(&c->bar_gen) == g) {
+        __nanosleep(100);
+        if (globaltimer() - t0 > timeout_ns) {
+          set_status(c, AGG_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    S.ok = ok;
+  }
+  __syncthreads();
+  return S.ok != 0;
+}
+
+// ---------------------------------------------------------------- table access
+
+template <int ENT>
+struct Ent {
+  static constexpr uint32_t ES = ENT == ENT64 ? 64u : 32u;
+  static constexpr bool MM = ENT != ENT32_CS;
+  __device__ static uint8_t* at(uint8_t* base, uint32_t slot) { return base + (size_t)slot * ES; }
+  __device__ static void add(uint8_t* e, uint32_t ops, unsigned long long c, unsigned long long s, long long mn,
+                             long long mx) {
+    if (ops & AGG_COUNT) atomicAdd(reinterpret_cast<unsigned long long*>(e + 8), c);
+    if (ops & AGG_SUM) atomicAdd(reinterpret_cast<unsigned long long*>(e + 16), s);
+    if (ENT == ENT32_CSMM32) {
+      if (ops & AGG_MIN) atomicMin(reinterpret_cast<int*>(e + 24), (int)mn);
+      if (ops & AGG_MAX) atomicMax(reinterpret_cast<int*>(e + 28), (int)mx);
+    } else if (ENT == ENT64) {
+      if (ops & AGG_MIN) atomicMin(reinterpret_cast<long long*>(e + 24), mn);
+      if (ops & AGG_MAX) atomicMax(reinterpret_cast<long long*>(e + 32), mx);
+    }
+  }
+  __device__ static void reset(uint8_t* e) {
+    __stcg(reinterpret_cast<unsigned long long*>(e + 8), 0ull);
+    __stcg(reinterpret_cast<unsigned long long*>(e + 16), 0ull);
+    if (ENT == ENT32_CSMM32) {
+      __stcg(reinterpret_cast<int*>(e + 24), INT32_MAX);
+      __stcg(reinterpret_cast<int*>(e + 28), INT32_MIN);
+    } else if (ENT == ENT64) {
+      __stcg(reinterpret_cast<long long*>(e + 24), (long long)INT64_MAX);
+      __stcg(reinterpret_cast<long long*>(e + 32), (long long)INT64_MIN);
+    }
+  }
+  __device__ static void read(uint8_t* e, long long& key, unsigned long long& c, unsigned long long& s, long long& mn,
+                              long long& mx) {
+    key = __ldcg(reinterpret_cast<const long long*>(e));
+    c = __ldcg(reinterpret_cast<const unsigned long long*>(e + 8));
+    s = __ldcg(reinterpret_cast<const unsigned long long*>(e + 16));
+    if (ENT == ENT32_CSMM32) {
+      mn = __ldcg(reinterpret_cast<const int*>(e + 24));
+      mx = __ldcg(reinterpret_cast<const int*>(e + 28));
+    } else if (ENT == ENT64) {
+      mn = __ldcg(reinterpret_cast<const long long*>(e + 24));
+      mx = __ldcg(reinterpret_cast<const long long*>(e + 32));
+    } else {
+      mn = mx = 0;
+    }
+  }
+};
+
+// Waits (bounded) until byte j of a tag word is no longer BUSY; returns the word.
+__device__ uint32_t wait_not_busy(const uint32_t* wp, uint32_t j, const HashParams& P) {
+  const uint64_t t0 = globaltimer();
+  uint32_t w;
+  while (true) {
+    w = ld_acquire_u32(wp);
+    if (((w >> (8 * j)) & 0xFFu) != TAG_BUSY) return w;
+    __nanosleep(20);
+    if (globaltimer() - t0 > P.timeout_ns) {
+      set_status(P.ctrl, AGG_ERR_TIMEOUT);
+      return w & ~(0xFFu << (8 * j)) | (TAG_CLOSED << (8 * j));  // give up: treat as closed
+    }
+  }
+}
+
+// Finds or claims the slot of `key`.  Returns the slot when the key is (now)
+// resident, -1 when the key must spill (chain closed, table full, or the probe
+// window holds only other keys).  *claimed is set when this call inserted it.
+template <int ENT>
+__device__ long long probe_table(const HashParams& P, uint32_t s_act, long long key, uint64_t h, bool full,
+                                 uint32_t& claimed) {
+  uint32_t pos = (uint32_t)(((h >> 32) * (uint64_t)s_act) >> 32);
+  const uint32_t tag = 0x80u | (uint32_t)(h & 0x7Fu);
+  uint32_t* tags = P.tags;
+  int steps = 0;
+  while (steps < MAX_PROBE) {
+    const uint32_t widx = pos >> 2;
+    uint32_t w = ld_acquire_u32(tags + widx);
+    for (uint32_t j = pos & 3u; j < 4 && steps < MAX_PROBE; ++j, ++steps) {
+      for (int attempt = 0;; ++attempt) {
+        const uint32_t b = (w >> (8 * j)) & 0xFFu;
+        const uint32_t slot = widx * 4 + j;
+        if (b == tag) {
+          const long long k2 = __ldcg(reinterpret_cast<const long long*>(Ent<ENT>::at(P.ent, slot)));
+          if (k2 == key) return slot;
+          break;
+        }
+        if (b >= 0x80u) break;
+        if (b == TAG_CLOSED) return -1;
+        if (b == TAG_BUSY) {
+          w = wait_not_busy(tags + widx, j, P);
+          continue;
+        }
+        // EMPTY: claim it for the key, or close the chain when the table is full.
+        const uint32_t nbyte = full ? TAG_CLOSED : TAG_BUSY;
+        const uint32_t nw = (w & ~(0xFFu << (8 * j))) | (nbyte << (8 * j));
+        const uint32_t old = atomicCAS(tags + widx, w, nw);
+        if (old != w) {
+          if (attempt > (1 << 16)) {
+            set_status(P.ctrl, AGG_ERR_TIMEOUT);
+            return -1;
+          }
+          w = ld_acquire_u32(tags + widx);
+          continue;
+        }
+        if (full) return -1;
+        __stcg(reinterpret_cast<long long*>(Ent<ENT>::at(P.ent, slot)), key);
+        __threadfence();
+        atomicXor(tags + widx, (TAG_BUSY ^ tag) << (8 * j));
+        claimed = 1;
+        return slot;
+      }
+    }
+    pos = (widx + 1) * 4;
+    if (pos >= s_act) pos = 0;
+  }
+  return -1;
+}
+
+// ---------------------------------------------------------------- per-level context
+
+struct Level {
+  uint32_t level;
+  uint64_t seed;
+  uint32_t s_act;     // active slots of this round
+  uint64_t cap;       // groups before the round's table counts as full
+  uint32_t dst;       // staging area receiving this level's spills
+  uint32_t fan_mask;
+};
+
+// Shared-memory cache probe; true when the key's partial state was updated.
+template <int ENT>
+__device__ __forceinline__ bool cache_hit(const Cache& cc, long long key, uint64_t h, unsigned long long c,
+                                          unsigned long long s, long long mn, long long mx) {
+  if (cc.n == 0 || key == SKEY_EMPTY) return false;
+  uint32_t idx = (uint32_t)(h >> 16) & (cc.n - 1);
+#pragma unroll 1
+  for (int i = 0; i < 8; ++i) {
+    const long long kk = *reinterpret_cast<volatile long long*>(cc.key + idx);
+    if (kk == key) {
+      atomicAdd(cc.cnt + idx, c);
+      atomicAdd(cc.sum + idx, s);
+      if (Ent<ENT>::MM) {
+        atomicMin(cc.mn + idx, mn);
+        atomicMax(cc.mx + idx, mx);
+      }
+      return true;
+    }
+    if (kk == SKEY_EMPTY) return false;
+    idx = (idx + 1) & (cc.n - 1);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void cache_insert(const Cache& cc, Smem& S, long long key, uint64_t h, uint32_t slot) {
+  if (cc.n == 0 || key == SKEY_EMPTY) return;
+  if (*reinterpret_cast<volatile uint32_t*>(&S.cache_used) >= cc.n / 2) return;
+  uint32_t idx = (uint32_t)(h >> 16) & (cc.n - 1);
+#pragma unroll 1
+  for (int i = 0; i < 8; ++i) {
+    const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(cc.key + idx),
+                                             (unsigned long long)SKEY_EMPTY, (unsigned long long)key);
+    if (old == (unsigned long long)SKEY_EMPTY) {
+      cc.slot[idx] = slot;
+      atomicAdd(&S.cache_used, 1u);
+      return;
+    }
+    if ((long long)old == key) return;
+    idx = (idx + 1) & (cc.n - 1);
+  }
+}
+
+template <int ENT>
+__device__ void cache_flush(const HashParams& P, const Cache& cc, Smem& S) {
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < cc.n; i += THREADS) {
+    const long long k = cc.key[i];
+    if (k == SKEY_EMPTY) continue;
+    const unsigned long long c = cc.cnt[i];
+    if (c) {
+      Ent<ENT>::add(Ent<ENT>::at(P.ent, cc.slot[i]), P.ops, c, cc.sum[i], Ent<ENT>::MM ? cc.mn[i] : 0,
+                    Ent<ENT>::MM ? cc.mx[i] : 0);
+    }
+    cc.key[i] = SKEY_EMPTY;
+    cc.cnt[i] = 0;
+    cc.sum[i] = 0;
+    if (Ent<ENT>::MM) {
+      cc.mn[i] = INT64_MAX;
+      cc.mx[i] = INT64_MIN;
+    }
+  }
+  if (threadIdx.x == 0) S.cache_used = 0;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- one tile of rows
+
+// Aggregates up to RPT rows per thread (block-uniform call), then spills the
+// rows whose keys are not resident.  `tile_row0` orders level-0 tiles.
+template <int ENT>
+__device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const Cache& cc, long long (&k)[RPT],
+                             long long (&v)[RPT], bool (&valid)[RPT], uint64_t tile_row0) {
+  const uint32_t lane = threadIdx.x & 31;
+  const bool full = S.full != 0;
+  uint32_t my_claims = 0;
+  bool sp[RPT];
+  uint32_t part[RPT];
+  bool any_sp = false;
+
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const bool val = valid[r];
+    const uint64_t h = fmix64((uint64_t)k[r] ^ L.seed);
+    uint32_t peers = 1u << lane;
+    uint32_t leader = lane;
+    unsigned long long gc = 1, gs = (unsigned long long)v[r];
+    long long gmn = v[r], gmx = v[r];
+    if (P.dedup) {
+      const uint32_t vm = __ballot_sync(FULL_MASK, val);
+      if (val) peers = __match_any_sync(vm, k[r]);
+      leader = __ffs(peers) - 1;
+      const uint32_t gsize = __popc(peers);
+      const uint32_t maxg = __reduce_max_sync(FULL_MASK, gsize);
+      if (maxg > 1) {
+        uint32_t rem = (val && lane == leader) ? (peers & ~(1u << lane)) : 0u;
+        for (uint32_t it = 1; it < maxg; ++it) {
+          const int src = rem ? __ffs(rem) - 1 : (int)lane;
+          rem &= rem - 1;
+          const long long ov = __shfl_sync(FULL_MASK, v[r], src);
+          if (src != (int)lane) {
+            gs += (unsigned long long)ov;
+            gmn = ov < gmn ? ov : gmn;
+            gmx = ov > gmx ? ov : gmx;
+          }
+        }
+        gc = gsize;
+      }
+    }
+    bool resident = true;
+    if (val && lane == leader) {
+      if (!cache_hit<ENT>(cc, k[r], h, gc, gs, gmn, gmx)) {
+        uint32_t claimed = 0;
+        const long long slot = probe_table<ENT>(P, L.s_act, k[r], h, full, claimed);
+        if (slot >= 0) {
+          Ent<ENT>::add(Ent<ENT>::at(P.ent, (uint32_t)slot), P.ops, gc, gs, gmn, gmx);
+          my_claims += claimed;
+          cache_insert(cc, S, k[r], h, (uint32_t)slot);
+        } else {
+          resident = false;
+        }
+      }
+    }
+    if (P.dedup) resident = __shfl_sync(FULL_MASK, resident, leader);
+    sp[r] = val && !resident;
+    part[r] = (uint32_t)(h >> 8) & L.fan_mask;
+    any_sp |= sp[r];
+  }
+
+  // ---- tile epilogue: publish claims, update the full flag
+  if (my_claims) atomicAdd(&S.claims, my_claims);
+  const int any = __syncthreads_or(any_sp);
+  if (threadIdx.x == 0) {
+    const uint32_t cl = S.claims;
+    S.claims = 0;
+    const unsigned long long occ =
+        cl ? atomicAdd(&P.ctrl->occupancy, (unsigned long long)cl) + cl : ld_relaxed_u64(&P.ctrl->occupancy);
+    if (!S.full && occ >= L.cap) {
+      S.full = 1;
+      if (L.level == 0) atomicMin(&P.ctrl->rows_at_full, (unsigned long long)tile_row0);
+    }
+  }
+  if (!any) {
+    __syncthreads();
+    return;
+  }
+
+  // ---- spill: warp-aggregated ranks per partition
+  uint32_t rank[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const uint32_t vm = __ballot_sync(FULL_MASK, sp[r]);
+    rank[r] = 0;
+    if (sp[r]) {
+      const uint32_t pm = __match_any_sync(vm, part[r]);
+      const int ldr = __ffs(pm) - 1;
+      uint32_t base = 0;
+      if ((int)lane == ldr) base = atomicAdd(&S.cnt[part[r]], (uint32_t)__popc(pm));
+      base = __shfl_sync(pm, base, ldr);
+      rank[r] = base + __popc(pm & lanemask_lt());
+    }
+  }
+  __syncthreads();
+  const uint32_t fan = L.fan_mask + 1;
+  const uint32_t dst = L.dst;
+  for (uint32_t p = threadIdx.x; p < fan; p += THREADS) {
+    const uint32_t c = S.cnt[p];
+    if (c == 0) continue;
+    const uint32_t f = S.fill[p];
+    if (f + c > CH) {  // this tile overflows the current chunk: open a new one
+      uint32_t nc = NONE;
+      const unsigned long long id = atomicAdd(&P.ctrl->pool_next[dst], 1ull);
+      if (id < P.max_chunks[dst]) {
+        nc = (uint32_t)id;
+        P.dir_part[dst][nc] = p;
+      } else {
+        set_status(P.ctrl, AGG_ERR_STAGING_EXHAUSTED);
+      }
+      if (S.cur[p] != NONE) P.dir_count[dst][S.cur[p]] = CH;
+      S.nxt[p] = nc;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    if (!sp[r]) continue;
+    const uint32_t p = part[r];
+    const uint32_t pos = S.fill[p] + rank[r];
+    uint32_t chunk, at;
+    if (pos < CH) {
+      chunk = S.cur[p];
+      at = pos;
+    } else {
+      chunk = S.nxt[p];
+      at = pos - CH;
+    }
+    if (chunk == NONE) continue;
+    longlong2 rec;
+    rec.x = k[r];
+    rec.y = v[r];
+    __stcs(reinterpret_cast<longlong2*>(P.stg[dst] + ((size_t)chunk * CH + at) * REC_BYTES), rec);
+  }
+  __syncthreads();
+  for (uint32_t p = threadIdx.x; p < fan; p += THREADS) {
+    const uint32_t c = S.cnt[p];
+    if (c == 0) continue;
+    const uint32_t f = S.fill[p];
+    if (f + c > CH) {
+      S.cur[p] = S.nxt[p];
+      S.fill[p] = f + c - CH;
+    } else {
+      S.fill[p] = f + c;
+    }
+    S.cnt[p] = 0;
+    atomicAdd(&S.spilled, (unsigned long long)c);
+  }
+  __syncthreads();
+}
+
+// Closes every open staging chunk of this block (writes its record count).
+__device__ void finalize_chunks(const HashParams& P, Smem& S, uint32_t dst, uint32_t level) {
+  __syncthreads();
+  for (uint32_t p = threadIdx.x; p < MAX_FAN; p += THREADS) {
+    if (S.cur[p] != NONE) P.dir_count[dst][S.cur[p]] = S.fill[p];
+    S.cur[p] = NONE;
+    S.fill[p] = CH;
+    S.cnt[p] = 0;
+  }
+  if (threadIdx.x == 0) {
+    if (S.spilled) atomicAdd(&P.ctrl->spill_records[level], S.spilled);
+    S.spilled = 0;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- emit
+
+__device__ uint32_t block_exclusive_scan(uint32_t x, uint32_t& total, Smem& S) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL_MASK, inc, o);
+    if ((int)lane >= o) inc += y;
+  }
+  if (lane == 31) S.warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = lane < WARPS ? S.warp_tot[lane] : 0;
+    uint32_t ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL_MASK, ti, o);
+      if ((int)lane >= o) ti += y;
+    }
+    if (lane < WARPS) S.warp_tot[lane] = ti - t;  // exclusive
+    if (lane == WARPS - 1) S.scan_total = ti;
+  }
+  __syncthreads();
+  total = S.scan_total;
+  const uint32_t r = S.warp_tot[warp] + inc - x;
+  __syncthreads();
+  return r;
+}
+
+// Writes every occupied slot of the active table to the output and resets it.
+template <int ENT>
+__device__ void emit_table(const HashParams& P, uint32_t s_act, uint32_t level, Smem& S) {
+  const uint32_t words = s_act / 4;
+  constexpr uint32_t WPT = 4;  // tag words per thread
+  const uint32_t seg_words = THREADS * WPT;
+  for (uint32_t seg = blockIdx.x; (uint64_t)seg * seg_words < words; seg += gridDim.x) {
+    const uint32_t w0 = seg * seg_words + threadIdx.x * WPT;
+    uint32_t tw[WPT];
+    uint32_t oc = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < WPT; ++q) {
+      tw[q] = (w0 + q < words) ? __ldcg(P.tags + w0 + q) : 0u;
+      oc += __popc(tw[q] & 0x80808080u);
+    }
+    uint32_t total;
+    const uint32_t off = block_exclusive_scan(oc, total, S);
+    if (threadIdx.x == 0) {
+      S.scan_base = total ? atomicAdd(&P.ctrl->out_count, (unsigned long long)total) : 0ull;
+      if (total) atomicAdd(&P.ctrl->resident_groups[level], (unsigned long long)total);
+    }
+    __syncthreads();
+    unsigned long long pos = S.scan_base + off;
+#pragma unroll
+    for (uint32_t q = 0; q < WPT; ++q) {
+      if (tw[q] == 0) continue;
+#pragma unroll
+      for (uint32_t j = 0; j < 4; ++j) {
+        const uint32_t b = (tw[q] >> (8 * j)) & 0xFFu;
+        if (b < 0x80u) continue;
+        uint8_t* e = Ent<ENT>::at(P.ent, (w0 + q) * 4 + j);
+        long long key, mn, mx;
+        unsigned long long c, s;
+        Ent<ENT>::read(e, key, c, s, mn, mx);
+        if (pos < P.o_cap) {
+          P.o_keys[pos] = key;
+          if (P.o_count) P.o_count[pos] = c;
+          if (P.o_sum) P.o_sum[pos] = (long long)s;
+          if (P.o_min) P.o_min[pos] = mn;
+          if (P.o_max) P.o_max[pos] = mx;
+        } else {
+          set_status(P.ctrl, AGG_ERR_OUTPUT_CAPACITY);
+        }
+        ++pos;
+        Ent<ENT>::reset(e);
+      }
+      __stcg(P.tags + w0 + q, 0u);
+    }
+    __syncthreads();
+  }
+}
+
+// Last block to arrive publishes the group count and the run's statistics,
+// then zeroes the per-run control fields for the next run.
+__device__ void final_step(const HashParams& P, uint32_t levels) {
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  Ctrl* C = P.ctrl;
+  __threadfence();
+  const uint32_t prev = atomicAdd(&C->done_count, 1u);
+  if (prev != gridDim.x - 1) return;
+  __threadfence();
+  volatile Ctrl* V = C;
+  const unsigned long long ng = V->out_count;
+  if (P.o_ngroups) *P.o_ngroups = ng;
+  C->last_n_rows = P.n;
+  C->last_n_groups = ng;
+  C->last_levels = levels;
+  C->last_rounds = V->rounds;
+  C->last_rows_at_full = V->rows_at_full;
+  for (int l = 0; l < AGG_MAX_LEVELS; ++l) {
+    C->last_spill_records[l] = V->spill_records[l];
+    C->last_resident_groups[l] = V->resident_groups[l];
+    C->spill_records[l] = 0;
+    C->resident_groups[l] = 0;
+  }
+  C->occupancy = 0;
+  C->out_count = 0;
+  C->pool_next[0] = 0;
+  C->pool_next[1] = 0;
+  C->rows_at_full = ~0ull;
+  C->rounds = 0;
+  for (int s = 0; s < 2; ++s)
+    for (int p = 0; p < MAX_FAN; ++p) {
+      C->part_records[s][p] = 0;
+      C->part_chunks[s][p] = 0;
+      C->part_cursor[s][p] = 0;
+    }
+  __threadfence();
+  C->done_count = 0;
+}
+
+// ---------------------------------------------------------------- the kernel
+
+template <int ENT, int VT>
+__global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  const Cache cc = carve_cache(smem_raw + ((sizeof(Smem) + 15) & ~size_t(15)), P.ns, Ent<ENT>::MM);
+  Ctrl* C = P.ctrl;
+  const uint32_t fan = 1u << P.fan_log2;
+
+  for (uint32_t p = threadIdx.x; p < MAX_FAN; p += THREADS) {
+    S.cnt[p] = 0;
+    S.cur[p] = NONE;
+    S.fill[p] = CH;
+    S.hrec[p] = 0;
+  }
+  for (uint32_t i = threadIdx.x; i < cc.n; i += THREADS) {
+    cc.key[i] = SKEY_EMPTY;
+    cc.cnt[i] = 0;
+    cc.sum[i] = 0;
+    if (Ent<ENT>::MM) {
+      cc.mn[i] = INT64_MAX;
+      cc.mx[i] = INT64_MIN;
+    }
+  }
+  if (threadIdx.x == 0) {
+    S.claims = 0;
+    S.full = 0;
+    S.cache_used = 0;
+    S.spilled = 0;
+  }
+  __syncthreads();
+
+  // ================= level 0: the input stream
+  {
+    Level L;
+    L.level = 0;
+    L.seed = level_seed(P.seed, 0);
+    L.s_act = P.s_act0;
+    L.cap = (uint64_t)(P.lf * (double)P.s_act0);
+    L.dst = 0;
+    L.fan_mask = fan - 1;
+    const uint64_t ntiles = (P.n + TILE - 1) / TILE;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const uint64_t row0 = t * TILE;
+      long long k[RPT], v[RPT];
+      bool valid[RPT];
+#pragma unroll
+      for (int j = 0; j < RPT / 2; ++j) {
+        const uint64_t row = row0 + (uint64_t)j * 2 * THREADS + 2 * threadIdx.x;
+        if (P.vec_ok && row + 1 < P.n) {
+          const longlong2 kk = __ldcs(reinterpret_cast<const longlong2*>(P.keys + row));
+          k[2 * j] = kk.x;
+          k[2 * j + 1] = kk.y;
+          if (!P.has_vals) {
+            v[2 * j] = v[2 * j + 1] = 0;
+          } else if (VT == AGG_I64) {
+            const longlong2 vv = __ldcs(reinterpret_cast<const longlong2*>(static_cast<const long long*>(P.vals) + row));
+            v[2 * j] = vv.x;
+            v[2 * j + 1] = vv.y;
+          } else {
+            const int2 vv = __ldcs(reinterpret_cast<const int2*>(static_cast<const int*>(P.vals) + row));
+            v[2 * j] = vv.x;
+            v[2 * j + 1] = vv.y;
+          }
+          valid[2 * j] = valid[2 * j + 1] = true;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const uint64_t rr = row + e;
+            valid[2 * j + e] = rr < P.n;
+            k[2 * j + e] = 0;
+            v[2 * j + e] = 0;
+            if (rr < P.n) {
+              k[2 * j + e] = __ldcs(reinterpret_cast<const long long*>(P.keys) + rr);
+              if (P.has_vals)
+                v[2 * j + e] = VT == AGG_I64 ? __ldcs(static_cast<const long long*>(P.vals) + rr)
+                                             : (long long)__ldcs(static_cast<const int*>(P.vals) + rr);
+            }
+          }
+        }
+      }
+      process_rows<ENT>(P, L, S, cc, k, v, valid, row0);
+    }
+    cache_flush<ENT>(P, cc, S);
+    finalize_chunks(P, S, 0, 0);
+    if (!grid_barrier(C, P.timeout_ns, S)) return;
+    const unsigned long long spilled = ld_relaxed_u64(&C->pool_next[0]);
+    emit_table<ENT>(P, L.s_act, 0, S);
+    if (threadIdx.x == 0 && blockIdx.x == 0) C->occupancy = 0;
+    if (spilled == 0) {
+      final_step(P, 1);
+      return;
+    }
+    if (!grid_barrier(C, P.timeout_ns, S)) return;
+  }
+
+  // ================= levels 1..: recursive processing of spilled partitions
+  for (uint32_t level = 1;; ++level) {
+    if (level >= AGG_MAX_LEVELS) {
+      if (threadIdx.x == 0 && blockIdx.x == 0) set_status(C, AGG_ERR_INTERNAL);
+      final_step(P, level);
+      return;
+    }
+    const uint32_t src = (level + 1) & 1, dst = level & 1, set = level & 1;
+    uint32_t* dpart = P.dir_part[src];
+    uint32_t* dcount = P.dir_count[src];
+    uint32_t* list = P.list[src];
+    // P1: per-partition chunk and record counts of the source area
+    if (threadIdx.x == 0 && blockIdx.x == 0) C->pool_next[dst] = 0;
+    const unsigned long long nch = ld_relaxed_u64(&C->pool_next[src]);
+    for (uint32_t p = threadIdx.x; p < MAX_FAN; p += THREADS) {
+      S.cnt[p] = 0;
+      S.hrec[p] = 0;
+    }
+    __syncthreads();
+    for (unsigned long long c = blockIdx.x * (unsigned long long)THREADS + threadIdx.x; c < nch;
+         c += (unsigned long long)gridDim.x * THREADS) {
+      const uint32_t p = __ldcg(dpart + c);
+      atomicAdd(&S.cnt[p], 1u);
+      atomicAdd(&S.hrec[p], (unsigned long long)__ldcg(dcount + c));
+    }
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < fan; p += THREADS) {
+      if (S.cnt[p]) {
+        atomicAdd(&C->part_chunks[set][p], S.cnt[p]);
+        atomicAdd(&C->part_records[set][p], S.hrec[p]);
+      }
+      S.cnt[p] = 0;
+    }
+    if (!grid_barrier(C, P.timeout_ns, S)) return;
+    // P3: chunk lists grouped by partition
+    if (threadIdx.x == 0) {
+      uint32_t acc = 0;
+      for (uint32_t p = 0; p < fan; ++p) {
+        S.begin[p] = acc;
+        acc += __ldcg(&C->part_chunks[set][p]);
+      }
+      S.begin[fan] = acc;
+    }
+    __syncthreads();
+    for (unsigned long long c = blockIdx.x * (unsigned long long)THREADS + threadIdx.x; c < nch;
+         c += (unsigned long long)gridDim.x * THREADS) {
+      const uint32_t p = __ldcg(dpart + c);
+      const uint32_t at = atomicAdd(&C->part_cursor[set][p], 1u);
+      list[S.begin[p] + at] = (uint32_t)c;
+    }
+    if (!grid_barrier(C, P.timeout_ns, S)) return;
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+      for (uint32_t p = 0; p < MAX_FAN; ++p) {
+        C->part_records[set ^ 1][p] = 0;
+        C->part_chunks[set ^ 1][p] = 0;
+        C->part_cursor[set ^ 1][p] = 0;
+      }
+    }
+    // Rounds: consecutive partitions packed while their records fit the table.
+    const uint64_t cap_full = (uint64_t)(P.lf * (double)P.slots);
+    uint32_t p = 0;
+    while (true) {
+      while (p < fan && __ldcg(&C->part_records[set][p]) == 0) ++p;
+      if (p >= fan) break;
+      uint64_t tot = __ldcg(&C->part_records[set][p]);
+      uint32_t q = p + 1;
+      while (q < fan) {
+        const uint64_t r = __ldcg(&C->part_records[set][q]);
+        if (tot + r > cap_full) break;
+        tot += r;
+        ++q;
+      }
+      Level L;
+      L.level = level;
+      L.seed = level_seed(P.seed, level);
+      uint64_t want = (uint64_t)((double)tot / P.lf) + 4;
+      want = (want + 3) & ~3ull;
+      if (want < MIN_SLOTS) want = MIN_SLOTS;
+      if (want > P.slots) want = P.slots;
+      L.s_act = (uint32_t)want;
+      L.cap = (uint64_t)(P.lf * (double)L.s_act);
+      L.dst = dst;
+      L.fan_mask = fan - 1;
+      if (threadIdx.x == 0) S.full = 0;
+      __syncthreads();
+      const uint32_t c0 = S.begin[p], c1 = S.begin[q];
+      const uint64_t nrec_slots = (uint64_t)(c1 - c0) * CH;
+      const uint64_t ntiles = (nrec_slots + TILE - 1) / TILE;
+      for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        long long k[RPT], v[RPT];
+        bool valid[RPT];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          const uint64_t g = t * TILE + (uint64_t)r * THREADS + threadIdx.x;
+          valid[r] = false;
+          k[r] = 0;
+          v[r] = 0;
+          if (g < nrec_slots) {
+            const uint32_t ci = c0 + (uint32_t)(g / CH);
+            const uint32_t off = (uint32_t)(g % CH);
+            const uint32_t chunk = __ldcg(list + ci);
+            if (off < __ldcg(dcount + chunk)) {
+              const longlong2 rec = __ldcs(reinterpret_cast<const longlong2*>(
+                  P.stg[src] + ((size_t)chunk * CH + off) * REC_BYTES));
+              k[r] = rec.x;
+              v[r] = rec.y;
+              valid[r] = true;
+            }
+          }
+        }
+        process_rows<ENT>(P, L, S, cc, k, v, valid, 0);
+      }
+      cache_flush<ENT>(P, cc, S);
+      if (!grid_barrier(C, P.timeout_ns, S)) return;
+      emit_table<ENT>(P, L.s_act, level, S);
+      if (threadIdx.x == 0 && blockIdx.x == 0) {
+        C->occupancy = 0;
+        C->rounds += 1;
+      }
+      if (!grid_barrier(C, P.timeout_ns, S)) return;
+      p = q;
+    }
+    finalize_chunks(P, S, dst, level);
+    if (!grid_barrier(C, P.timeout_ns, S)) return;
+    if (ld_relaxed_u64(&C->pool_next[dst]) == 0) {
+      final_step(P, level + 1);
+      return;
+    }
+  }
+}
+
+template <int ENT>
+__global__ void init_table_kernel(uint8_t* ent, uint32_t* tags, uint32_t slots) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < slots; s += (uint64_t)gridDim.x * blockDim.x) {
+    uint8_t* e = Ent<ENT>::at(ent, (uint32_t)s);
+    *reinterpret_cast<long long*>(e) = 0;
+    Ent<ENT>::reset(e);
+    if ((s & 3) == 0) tags[s >> 2] = 0;
+  }
+}
+
+template <int ENT, int VT>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(&hash_groupby_kernel<ENT, VT>);
+}
+
+void* pick_kernel(int ent, int vt) {
+  if (vt == AGG_I32) {
+    if (ent == ENT32_CS) return kernel_ptr<ENT32_CS, AGG_I32>();
+    if (ent == ENT32_CSMM32) return kernel_ptr<ENT32_CSMM32, AGG_I32>();
+    return kernel_ptr<ENT64, AGG_I32>();
+  }
+  if (ent == ENT32_CS) return kernel_ptr<ENT32_CS, AGG_I64>();
+  return kernel_ptr<ENT64, AGG_I64>();
+}
+
+size_t smem_bytes(int ent, uint32_t ns) {
+  return ((sizeof(Smem) + 15) & ~size_t(15)) + cache_bytes(ns, ent != ENT32_CS);
+}
+
+}  // namespace
+
+cudaError_t hash_kernel_info(int ent_kind, int vt, uint32_t ns, int device, KernelInfo* out) {
+  void* k = pick_kernel(ent_kind, vt);
+  const size_t smem = smem_bytes(ent_kind, ns);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, THREADS, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  out->blocks = per_sm * sms;
+  out->smem = smem;
+  return cudaSuccess;
+}
+
+cudaError_t hash_launch(int ent_kind, int vt, const HashParams& p, const KernelInfo& ki, cudaStream_t s) {
+  void* k = pick_kernel(ent_kind, vt);
+  void* args[] = {const_cast<HashParams*>(&p)};
+  return cudaLaunchCooperativeKernel(k, dim3(ki.blocks), dim3(THREADS), args, ki.smem, s);
+}
+
+cudaError_t hash_init_table(uint8_t* ent, uint32_t* tags, uint32_t slots, int ent_kind, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((slots + 255) / 256 > 4096 ? 4096 : (slots + 255) / 256);
+  if (ent_kind == ENT32_CS) init_table_kernel<ENT32_CS><<<blocks, 256, 0, s>>>(ent, tags, slots);
+  else if (ent_kind == ENT32_CSMM32) init_table_kernel<ENT32_CSMM32><<<blocks, 256, 0, s>>>(ent, tags, slots);
+  else init_table_kernel<ENT64><<<blocks, 256, 0, s>>>(ent, tags, slots);
+  return cudaGetLastError();
+}
+
+}  // namespace agg

@@ -1,0 +1,65 @@
+"""The C-ABI library loads and exports every entry point include/agg.h declares
+(no GPU needed: only host-side functions are called)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions(path):
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(agg_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1311_0059_gb300 import _abi
+    if not os.path.exists(_abi.LIB_PATH):
+        from paper_1311_0059_gb300 import build
+        build.build()
+    return _abi.load()
+
+
+def test_header_lists_the_boundary():
+    names = header_functions(os.path.join(ROOT, "include", "agg.h"))
+    for must in ("agg_create", "agg_run", "agg_destroy", "agg_sync", "agg_strerror"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1311_0059_gb300 import _abi
+    names = header_functions(os.path.join(ROOT, "include", "agg.h"))
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in agg.h but not exported"
+        assert n in _abi.SIGNATURES, f"{n} has no Python binding"
+
+
+def test_strerror(lib):
+    from paper_1311_0059_gb300 import _abi
+    for s in range(0, 9):
+        assert _abi.strerror(s)
+    assert _abi.strerror(0) == "ok"
+
+
+def test_plan_is_host_only_and_follows_the_budget(lib):
+    from paper_1311_0059_gb300 import groupby as gb, _abi
+    spec = gb.make_spec(ops=15, value_type=_abi.AGG_I64)
+    p = gb.plan(256 << 20, 200_000_000, spec)
+    assert p["entry_bytes"] == 64
+    assert p["working_bytes"] <= 256 << 20
+    assert p["table_slots"] * 65 <= 256 << 20
+    assert p["fan_out"] == 64            # 200M * 64 B * 1.2 / 256 MiB = 57.2 -> 64
+    spec32 = gb.make_spec(ops=15, value_type=_abi.AGG_I32)
+    assert gb.plan(64 << 20, 1_000_000, spec32)["entry_bytes"] == 32
+    assert gb.plan(1 << 30, 10, gb.make_spec(ops=3))["fan_out"] == 16
+    with pytest.raises(_abi.AggError) as e:
+        gb.plan(1000, 10, spec)
+    assert e.value.status == _abi.AGG_ERR_BUDGET_TOO_SMALL
+    bad = gb.make_spec(ops=0)
+    with pytest.raises(_abi.AggError) as e:
+        gb.plan(1 << 20, 10, bad)
+    assert e.value.status == _abi.AGG_ERR_INVALID_ARG

@@ -78,3 +78,9 @@ def test_zipf_frequencies():
 def test_instance_seeds_distinct():
     s = [dg.instance_seed(0, i) for i in range(10_000)]
     assert len(set(s)) == len(s)
+
+
+def test_rank_of_key_inverts_key_of_rank():
+    r = np.concatenate([np.arange(1000, dtype=np.uint64), np.array([2**64 - 1, 2**63, 12345678901234], np.uint64)])
+    for seed in (0, 7):
+        assert np.array_equal(dg.rank_of_key(seed, dg.key_of_rank(seed, r)), r)
