@@ -1,0 +1,420 @@
+"""Benchmark of the budgeted group-by on GB300 (one JSON line on stdout).
+
+A step is one agg_run of the hash path over one batch of synthetic rows already
+resident in HBM.  The default workload is the spilling hybrid-hash group-by:
+200M rows, int64 keys uniform over a 50M-key domain, int64 values in
+[0, 2^20), COUNT+SUM+MIN+MAX, 256 MB working-memory budget, so groups overflow
+the table, spill, and recurse.  The same input also runs through the radix-sort
+path for comparison.  Inputs (3.2 GB) exceed the 129 MB L2, so no flush is needed
+between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload spill|plain|zipf] [--rows R --domain D --budget B]
+
+Under torchrun (N > 1) every rank runs an independent instance of the workload
+(its own seed) on its own GPU: the work shards with no data-path collective,
+scaling is weak, and `value` is the total rows of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import datagen as dg  # noqa: E402
+
+WORKLOADS = {"spill": dg.SPILL_200M_50M, "plain": dg.PLAIN_1M_10K, "zipf": dg.ZIPF_500M_10M}
+L2_BYTES = 129 << 20
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="spill", choices=sorted(WORKLOADS))
+    ap.add_argument("--rows", type=int, default=0)
+    ap.add_argument("--domain", type=int, default=0)
+    ap.add_argument("--budget", type=int, default=0)
+    ap.add_argument("--no-sort", action="store_true", help="skip the sort-path comparison leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the oracle sample (default: by workload)")
+    return ap.parse_args(argv)
+
+
+def workload(args, rank=0) -> dg.Workload:
+    base = WORKLOADS[args.workload]
+    w = dg.Workload(base.name, n=args.rows or base.n, domain=args.domain or base.domain, dist=base.dist,
+                    zipf_s=base.zipf_s, vtype=base.vtype, seed=base.seed + rank, budget=args.budget or base.budget,
+                    ops=base.ops)
+    if args.rows or args.domain or args.budget:
+        w.name = f"{w.dist} {w.n} rows over {w.domain} keys, budget {w.budget >> 20} MiB"
+    return w
+
+
+def config_of(w: dg.Workload, n_gpus: int) -> dict:
+    return {"workload": w.name, "rows": w.n, "key_domain": w.domain, "distribution": w.dist,
+            "zipf_s": w.zipf_s if w.dist == "zipf" else None, "value_type": w.vtype, "budget_bytes": w.budget,
+            "ops": "COUNT,SUM,MIN,MAX" if w.ops == 15 else ("COUNT,SUM" if w.ops == 3 else str(w.ops)),
+            "global_batch": w.n * n_gpus, "parallelism": f"independent instance per GPU x{n_gpus}",
+            "l2": "inputs larger than L2, no flush" if w.n * 16 > 2 * L2_BYTES else "input copies rotated to defeat L2"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int, interval_ms: int = 50):
+        self.cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-i",
+                    str(device_index), "-lms", str(interval_ms)]
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1311_0059_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(workload_name)
+    if not ent or ent.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_sample(w: dg.Workload, rows: int):
+    """Times the CPU oracle (single thread) on the first `rows` rows of w."""
+    import oracle
+    keys, vals = w.host(0, rows)
+    o = oracle.default()
+    t0 = time.perf_counter()
+    res, runs = o.groupby(keys, vals, budget_bytes=w.budget)
+    dt = time.perf_counter() - t0
+    return dt, res["keys"].size, runs
+
+
+def default_cpu_rows(w: dg.Workload) -> int:
+    return min(w.n, 10_000_000)
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    w = workload(args)
+    rows = args.cpu_rows or min(w.n, 2_000_000)
+    for _ in range(args.warmup):
+        oracle_sample(w, rows)
+    times = []
+    for _ in range(args.steps):
+        dt, _, _ = oracle_sample(w, rows)
+        times.append(dt)
+    total = sum(times)
+    v = rows * args.steps / total
+    sample = f"first {rows} rows of the workload per step (same distribution and budget), single thread"
+    line = {"impl": "reference", "metric": "group-by rows/s", "value": v, "unit": "rows/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": config_of(w, world),
+            "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    from paper_1311_0059_gb300 import AGG_I32, AGG_I64, AGG_PATH_HASH, AGG_PATH_SORT
+    from paper_1311_0059_gb300.costmodel import predicted_spill_records
+    from paper_1311_0059_gb300.groupby import GroupBy
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args, rank)
+    vt = AGG_I32 if w.vtype == "i32_1000" else AGG_I64
+    stream = torch.cuda.current_stream()
+
+    # inputs resident in HBM before timing; small inputs are rotated across copies
+    copies = 1 if w.n * 16 > 2 * L2_BYTES else max(2, (4 * L2_BYTES) // max(w.n * 12, 1) + 1)
+    keys, vals, cdf = [], [], None
+    for c in range(copies):
+        k = torch.empty(w.n, dtype=torch.int64, device=dev)
+        v = torch.empty(w.n, dtype=torch.int32 if vt == AGG_I32 else torch.int64, device=dev)
+        if w.dist == "zipf" and cdf is None:
+            cdf = torch.from_numpy(w.cdf()).to(dev)
+        w.device(k.data_ptr(), v.data_ptr(), cdf_ptr=cdf.data_ptr() if cdf is not None else 0,
+                 stream_handle=stream.cuda_stream)
+        keys.append(k)
+        vals.append(v)
+    torch.cuda.synchronize()
+
+    g = GroupBy(w.budget, ops=w.ops, value_type=vt, path=AGG_PATH_HASH)
+    g.reserve(w.n)
+    out = g.output(w.n, dev)
+
+    def step(i):
+        st = g.run_async(keys[i % copies], vals[i % copies], out, w.n, stream)
+        if st != 0:
+            raise RuntimeError(f"agg_run failed with status {st}")
+
+    for i in range(max(args.warmup, 1)):
+        step(i)
+    n_groups = g.sync()
+    st0 = g.stats()
+    launches0 = st0["kernel_launches"]
+
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for i in range(args.steps):
+            step(i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms_total = ev0.elapsed_time(ev1)
+    g.sync()
+    stats = g.stats()
+    gpu_launches = stats["kernel_launches"] - launches0
+    ms_max = max_over_ranks(ms_total, world, dev)
+    rows_total = sum_over_ranks(float(w.n * args.steps), world, dev)
+    value = rows_total / (ms_max / 1e3)
+
+    # algorithmic bytes of one launch: input + spill written + spill read + result
+    in_b = w.n * (8 + (4 if vt == AGG_I32 else 8))
+    spill_b = stats["spill_bytes_written"] + stats["spill_bytes_read"]
+    nagg = bin(w.ops).count("1")
+    out_b = n_groups * 8 * (1 + nagg)
+    alg_bytes = in_b + spill_b + out_b
+    kernel_ms = ms_total / args.steps  # one kernel launch per step
+    peak, peak_kind = measured_peak_gbs()
+    achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": recorded_traffic(w.name), "kernel": "hash_groupby_kernel", "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "bytes_breakdown": {"input": in_b, "spill_write": stats["spill_bytes_written"],
+                                "spill_read": stats["spill_bytes_read"], "result": out_b}}
+
+    # measured spill vs the Pre-Partitioning cost model (Section 5.3.4)
+    k_cap = stats["table_capacity"]
+    pred = predicted_spill_records(w.n, k_cap, n_groups)
+    spill = {"measured_records_level0": stats["spill_records"][0], "measured_bytes_total": spill_b,
+             "model_records_level0": pred, "model_bytes_level0": pred * 16, "K": k_cap, "G_t": n_groups,
+             "levels": stats["levels"], "rounds": stats["rounds"], "fan_out": stats["fan_out"]}
+
+    line = {"metric": "group-by rows/s (hash path, HBM-resident input)", "value": value, "unit": "rows/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded SplitMix64 generator, generated on the device)",
+            "config": config_of(w, world), "roofline": roof, "gpu_launches": gpu_launches,
+            "n_groups": n_groups, "spill": spill, "clocks": clocks.summary()}
+
+    # sort path on the same input
+    if not args.no_sort:
+        try:
+            gs = GroupBy(w.budget, ops=w.ops, value_type=vt, path=AGG_PATH_SORT)
+            gs.reserve(w.n)
+            outs = g.output(w.n, dev)
+            for i in range(2):
+                assert gs.run_async(keys[0], vals[0], outs, w.n, stream) == 0
+            ng_sort = gs.sync()
+            sk = max(3, min(10, args.steps))
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for i in range(sk):
+                assert gs.run_async(keys[i % copies], vals[i % copies], outs, w.n, stream) == 0
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            gs.sync()
+            sms = ev0.elapsed_time(ev1) / sk
+            line["sort_path"] = {"rows_per_s": w.n / (sms / 1e3), "ms_per_run": sms, "n_groups": ng_sort,
+                                 "same_group_count": ng_sort == n_groups, "steps": sk}
+            gs.close()
+            del outs
+        except Exception as e:  # the comparison leg must not hide the main number
+            line["sort_path"] = {"error": str(e)}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    if not args.no_e2e:
+        hk = torch.empty(w.n, dtype=torch.int64, pin_memory=True)
+        hv = torch.empty(w.n, dtype=vals[0].dtype, pin_memory=True)
+        hk.copy_(keys[0])
+        hv.copy_(vals[0])
+        cap = n_groups
+        hout = {f: torch.empty(cap, dtype=torch.int64, pin_memory=True) for f in ("keys", "count", "sum", "min",
+                                                                                     "max")}
+        import ctypes
+        from paper_1311_0059_gb300._abi import agg_output, check
+        ho = agg_output(keys=hout["keys"].data_ptr(), count=hout["count"].data_ptr(), sum=hout["sum"].data_ptr(),
+                        min=hout["min"].data_ptr(), max=hout["max"].data_ptr(), capacity=cap, d_n_groups=None)
+        ng = ctypes.c_uint64()
+        sp = ctypes.c_void_p(stream.cuda_stream)
+        for _ in range(2):
+            check(g.lib.agg_run_host(g.h, ctypes.c_void_p(hk.data_ptr()), ctypes.c_void_p(hv.data_ptr()), w.n,
+                                     ctypes.byref(ho), ctypes.byref(ng), sp), "agg_run_host")
+        ek = max(3, min(10, args.steps))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(ek):
+            check(g.lib.agg_run_host(g.h, ctypes.c_void_p(hk.data_ptr()), ctypes.c_void_p(hv.data_ptr()), w.n,
+                                     ctypes.byref(ho), ctypes.byref(ng), sp), "agg_run_host")
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e_rows = sum_over_ranks(float(w.n * ek), world, dev)
+        line["e2e"] = {"value": e2e_rows / dt, "unit": "rows/s", "h2d_bytes_per_step": in_b,
+                       "d2h_bytes_per_step": int(ng.value) * 8 * (1 + nagg) + 8, "steps": ek,
+                       "api": "agg_run_host (pinned host buffers)"}
+
+    if not args.no_cpu and rank == 0:
+        rows = args.cpu_rows or default_cpu_rows(w)
+        dt, ng_s, runs = oracle_sample(w, rows)
+        line["cpu_baseline"] = {"value": rows / dt, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {rows} rows of the same workload and budget "
+                                          f"({ng_s} groups, {runs} sorted runs), single-threaded C++ oracle",
+                                "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

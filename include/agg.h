@@ -78,7 +78,8 @@ typedef struct agg_spec {
 
 /* Knobs of the hash path; zero fields keep the defaults. */
 typedef struct agg_tuning {
-  double max_load_factor;  /* table fill before it counts as full (default 0.5); the
+  double max_load_factor;  /* planned fill of a recursion round's table (default 0.5):
+                              the round's slots are its records / max_load_factor; the
                               slot-table-size ratio of Section 6.7 is its inverse */
   uint32_t smem_entries;   /* per-block shared-memory pre-aggregation entries, power of
                               two 256..4096 (default 2048); 1 disables the cache */
@@ -113,14 +114,18 @@ typedef struct agg_stats {
   uint64_t resident_groups[AGG_MAX_LEVELS];      /* groups completed at level L */
   uint64_t spill_bytes_written;                  /* 16 B per spilled record */
   uint64_t spill_bytes_read;
-  uint64_t rows_at_full;                         /* level-0 rows seen when the table filled (~R_H) */
+  uint64_t rows_at_full;                         /* first level-0 row of a tile that spilled (~R_H) */
   uint64_t table_slots;
-  uint64_t table_capacity;                       /* groups held before the table counts as full (K) */
+  uint64_t table_capacity;                       /* planned groups per table, max_load_factor * slots (K) */
   uint64_t table_bytes;                          /* working memory used inside the budget */
   uint64_t budget_bytes;
   uint64_t staging_bytes;                        /* reserved staging (outside the budget) */
   uint64_t fan_out;
   uint64_t status_bits;                          /* 1 << agg_status of device-side errors seen */
+  uint64_t kernel_launches;                      /* kernels this handle has launched, cumulative */
+  uint64_t phase_ns[8];                          /* hash path, block 0's time per phase: level-0 pass,
+                                                    barrier wait, level-0 emit, partition lists, round
+                                                    aggregation, barrier waits, round emit, total */
 } agg_stats;
 
 /* Planner output (host-only arithmetic, no GPU needed). */

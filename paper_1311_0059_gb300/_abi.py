@@ -55,12 +55,14 @@ class agg_stats(ctypes.Structure):
                 ("spill_records", _U64 * AGG_MAX_LEVELS), ("resident_groups", _U64 * AGG_MAX_LEVELS),
                 ("spill_bytes_written", _U64), ("spill_bytes_read", _U64), ("rows_at_full", _U64),
                 ("table_slots", _U64), ("table_capacity", _U64), ("table_bytes", _U64), ("budget_bytes", _U64),
-                ("staging_bytes", _U64), ("fan_out", _U64), ("status_bits", _U64)]
+                ("staging_bytes", _U64), ("fan_out", _U64), ("status_bits", _U64), ("kernel_launches", _U64),
+                ("phase_ns", _U64 * 8)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
         d["spill_records"] = list(self.spill_records)
         d["resident_groups"] = list(self.resident_groups)
+        d["phase_ns"] = list(self.phase_ns)
         return d
 
 

@@ -45,6 +45,7 @@ struct agg_handle {
   SortState sort{};
   cudaStream_t last_stream = nullptr;
   bool ran = false;
+  uint64_t launches = 0;
 };
 
 namespace {
@@ -136,22 +137,25 @@ struct Layout {
   uint64_t ctrl_bytes, tags_off, ent_off, slots, total;
 };
 
+// Working memory: [control block][tag bytes: S + BUCKET][entries: S + 1].
+// Entry S is the side slot of the key value that marks empty slots.
 bool layout_for(size_t budget, uint32_t es, Layout* L) {
   L->ctrl_bytes = align_up(sizeof(Ctrl), 256);
   if (budget < AGG_MIN_BUDGET) return false;
-  uint64_t avail = budget - L->ctrl_bytes - 512;
-  uint64_t s = (avail / (es + 1)) & ~3ull;
-  if (s > (1ull << 31) - 4) s = (1ull << 31) - 4;
+  const uint64_t fixed = L->ctrl_bytes + BUCKET + es + 512;
+  uint64_t s = (budget - fixed) / (es + 1);
+  s -= s % BUCKET;
+  if (s > (1ull << 31) - BUCKET) s = (1ull << 31) - BUCKET;
   L->slots = s;
   L->tags_off = L->ctrl_bytes;
-  L->ent_off = align_up(L->tags_off + s, 256);
-  L->total = L->ent_off + s * es;
+  L->ent_off = align_up(L->tags_off + s + BUCKET, 256);
+  L->total = L->ent_off + (s + 1) * es;
   return s >= MIN_SLOTS && L->total <= budget;
 }
 
 uint32_t active_slots(uint64_t est, double lf, uint64_t slots) {
-  uint64_t want = (uint64_t)((double)est / lf) + 4;
-  want = (want + 3) & ~3ull;
+  uint64_t want = (uint64_t)((double)est / lf) + BUCKET;
+  want = (want + BUCKET - 1) / BUCKET * BUCKET;
   if (want < MIN_SLOTS) want = MIN_SLOTS;
   if (want > slots) want = slots;
   return (uint32_t)want;
@@ -286,6 +290,29 @@ agg_status agg_create(size_t budget, const agg_spec* spec, agg_handle** out) {
     delete h;
     return AGG_ERR_BUDGET_TOO_SMALL;
   }
+  if (spec->path == AGG_PATH_SORT) {
+    // sort path: the control block plus the sort's double buffers fill the budget
+    const uint64_t cb = align_up(sizeof(Ctrl), 256);
+    if (cudaMalloc(&h->work, cb) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return AGG_ERR_OOM;
+    }
+    h->ctrl = static_cast<Ctrl*>(h->work);
+    if (cudaMallocHost(&h->ng_host, 64) != cudaSuccess || cudaMemset(h->ctrl, 0, sizeof(Ctrl)) != cudaSuccess) {
+      cudaGetLastError();
+      agg_destroy(h);
+      return AGG_ERR_CUDA;
+    }
+    agg_status st = sort_reserve(h->sort, 0, budget - cb, *spec);
+    if (st != AGG_OK) {
+      agg_destroy(h);
+      return st;
+    }
+    h->working_bytes = cb + h->sort.work_bytes;
+    *out = h;
+    return AGG_OK;
+  }
   h->slots = L.slots;
   h->working_bytes = L.total;
   if (cudaMalloc(&h->work, L.total) != cudaSuccess) {
@@ -321,6 +348,10 @@ agg_status agg_set_tuning(agg_handle* h, const agg_tuning* t) {
   if (!h || !valid_tuning(t)) return AGG_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   const agg_tuning e = effective(t);
+  if (h->spec.path == AGG_PATH_SORT) {
+    h->tune = e;
+    return AGG_OK;
+  }
   KernelInfo ki;
   if (hash_kernel_info(h->ent_kind, h->spec.value_type, e.smem_entries > 1 ? e.smem_entries : 0, h->device, &ki) !=
       cudaSuccess) {
@@ -347,8 +378,7 @@ agg_status agg_reserve(agg_handle* h, uint64_t max_rows) {
   DeviceGuard g(h->device);
   const uint32_t fan = plan_fan(&h->spec, h->tune, max_rows, h->budget, h->es);
   if (h->spec.path == AGG_PATH_SORT) {
-    agg_status st = sort_reserve(h->sort, max_rows, h->budget, h->spec);
-    if (st != AGG_OK) return st;
+    return sort_reserve(h->sort, max_rows, h->budget - align_up(sizeof(Ctrl), 256), h->spec);
   }
   return reserve_staging(h, max_rows, fan);
 }
@@ -375,7 +405,12 @@ agg_status agg_run(agg_handle* h, const int64_t* d_keys, const void* d_vals, uin
     return AGG_ERR_INVALID_ARG;
 
   if (h->spec.path == AGG_PATH_SORT) {
-    agg_status st = sort_run(h->sort, h->budget, h->spec, h->ctrl, d_keys, d_vals, n, out, s);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      return AGG_ERR_INVALID_ARG;  // the sort path plans on the host between kernels
+    cudaGetLastError();
+    agg_status st = sort_run(h->sort, h->budget - align_up(sizeof(Ctrl), 256), h->spec, h->ctrl, d_keys, d_vals, n,
+                             out, s);
     h->last_stream = s;
     h->ran = true;
     return st;
@@ -428,6 +463,7 @@ agg_status agg_run(agg_handle* h, const int64_t* d_keys, const void* d_vals, uin
     cudaGetLastError();
     return AGG_ERR_CUDA;
   }
+  h->launches += 1;
   h->last_stream = s;
   h->ran = true;
   return AGG_OK;
@@ -487,7 +523,8 @@ agg_status agg_get_stats(agg_handle* h, agg_stats* s) {
   }
   s->spill_bytes_written = spilled * REC_BYTES;
   s->spill_bytes_read = spilled * REC_BYTES;
-  s->rows_at_full = c.last_rows_at_full;
+  s->rows_at_full = c.last_rows_at_full == ~0ull ? 0 : c.last_rows_at_full;
+  for (int i = 0; i < 8; ++i) s->phase_ns[i] = c.last_phase_ns[i];
   s->table_slots = h->slots;
   s->table_capacity = (uint64_t)(h->tune.max_load_factor * (double)h->slots);
   s->table_bytes = h->working_bytes;
@@ -495,6 +532,7 @@ agg_status agg_get_stats(agg_handle* h, agg_stats* s) {
   s->staging_bytes = h->staging_bytes + sort_staging_bytes(h->sort);
   s->fan_out = plan_fan(&h->spec, h->tune, c.last_n_rows, h->budget, h->es);
   s->status_bits = c.status_bits;
+  s->kernel_launches = h->launches + sort_launches(h->sort);
   if (h->spec.path == AGG_PATH_SORT) sort_fill_stats(h->sort, s);
   return AGG_OK;
 }

@@ -15,11 +15,12 @@ constexpr int RPT = 4;                     // rows per thread per tile
 constexpr int TILE = THREADS * RPT;        // rows per block tile
 constexpr uint32_t CH = 2048;              // records per staging chunk (32 KiB)
 constexpr int MAX_FAN = 256;               // largest spill fan-out
-constexpr int MAX_PROBE = 128;             // slots examined before a key counts as absent
+constexpr uint32_t BUCKET = 16;            // slots per bucket: one 16-byte load of tag bytes
 constexpr uint32_t MIN_SLOTS = 4096;       // smallest active table of a round
 constexpr uint32_t NONE = 0xFFFFFFFFu;
-constexpr uint32_t TAG_EMPTY = 0x00, TAG_CLOSED = 0x01, TAG_BUSY = 0x02;  // occupied: 0x80 | 7 hash bits
+constexpr int64_t EMPTY_KEY = INT64_MIN;   // empty key slot; this one key value lives in a side slot
 constexpr int64_t SKEY_EMPTY = INT64_MIN;  // empty marker of the shared-memory cache
+constexpr int PHASES = 8;                  // phase timers kept by block 0
 constexpr uint64_t REC_BYTES = 16;         // spilled record: (int64 key, int64 value)
 // One tile adds at most TILE rows to a partition, so at most one new chunk is
 // opened per partition per tile.
@@ -44,8 +45,9 @@ struct alignas(128) Ctrl {
   unsigned long long occupancy;    // slots claimed in the current round
   unsigned long long out_count;    // groups written so far
   unsigned long long pool_next[2]; // chunks handed out per staging area
-  unsigned long long rows_at_full; // level-0 row index when the table became full
+  unsigned long long rows_at_full; // level-0 row index of the first tile that spilled
   unsigned long long rounds;
+  unsigned long long phase_ns[PHASES];
   unsigned long long spill_records[AGG_MAX_LEVELS];
   unsigned long long resident_groups[AGG_MAX_LEVELS];
   unsigned long long part_records[2][MAX_FAN];
@@ -57,6 +59,7 @@ struct alignas(128) Ctrl {
   unsigned long long last_levels;
   unsigned long long last_rounds;
   unsigned long long last_rows_at_full;
+  unsigned long long last_phase_ns[PHASES];
   unsigned long long last_spill_records[AGG_MAX_LEVELS];
   unsigned long long last_resident_groups[AGG_MAX_LEVELS];
 };
@@ -78,7 +81,7 @@ struct HashParams {
   Ctrl* ctrl;
   uint8_t* ent;
   uint32_t* tags;
-  uint32_t slots;      // physical slots S (multiple of 4)
+  uint32_t slots;      // physical slots S (multiple of BUCKET); entry `slots` is the side slot
   uint8_t* stg[2];     // staging areas (chunks of CH records)
   uint32_t* dir_part[2];
   uint32_t* dir_count[2];

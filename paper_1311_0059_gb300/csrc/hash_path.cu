@@ -5,22 +5,26 @@
 // 6.7).  Duplicates inside a warp are combined first (match_any + shuffles),
 // then a per-block shared-memory cache of resident groups absorbs hot keys, and
 // the remaining updates go to the global open-addressing table with 64-bit
-// atomics.  The table follows the Pre-Partitioning policy (Section 4.3.4): new
-// groups are inserted until the table is full; afterwards a key that is not
-// resident is spilled, so every group is either completed in place or spilled
-// whole.  Spilled rows are radix-partitioned on hash bits into staging chunks
-// (the run files of Section 4.3) with warp-aggregated cursors.  After the pass
-// the table is emitted and reset.  Spilled partitions are then processed level
-// by level (Phase 2) with fresh seeds; small partitions are packed into one
-// table round (partition tuning, Section 4.3.3).  Phases are separated by grid
-// barriers whose waits are bounded.
+// atomics.  The table follows the Pre-Partitioning policy (Section 4.3.4):
+// every group that finds room in the table before the table is full is
+// resident and completes in place; a group that finds no room is spilled, and
+// it is spilled whole.  Spilled rows are radix-partitioned on hash bits into
+// staging chunks (the run files of Section 4.3) with warp-aggregated cursors.
+// After the pass the table is emitted and reset.  Spilled partitions are then
+// processed level by level (Phase 2) with fresh seeds; small partitions are
+// packed into one table round (partition tuning, Section 4.3.3).  Phases are
+// separated by grid barriers whose waits are bounded.
 //
-// Residency protocol.  One tag byte per slot is the synchronisation point:
-// EMPTY, CLOSED, BUSY or 0x80|7 hash bits.  An insert CASes EMPTY->BUSY on the
-// tag word, writes the key, fences, and turns BUSY into its tag.  Once the
-// table is full a lookup that reaches an EMPTY slot CASes it to CLOSED instead,
-// which ends that probe chain for good.  Exactly one of "insert k" and "close
-// k's chain" wins the CAS, so a key can never be both resident and spilled.
+// Table and residency.  Slots form buckets of 16; a key may live only in the
+// 32 slots of its two consecutive buckets (its window), filled in order.  A key
+// slot changes once per round, from EMPTY to a key, by a 64-bit atomicCAS, so
+// "k is absent and its window holds only other keys" can never become false
+// later in the round: such a key spills consistently, and a key is never both
+// resident and spilled.  "Full" (Section 3.2: no new group fits) is therefore
+// judged per window.  A tag byte per slot (0x80 | 7 hash bits, written after the
+// claim) is a compact filter kept in L2: probes compare 32 tags at once and
+// read keys only where a tag matches or is still zero.  The key value that
+// marks an empty slot (INT64_MIN) is kept in a dedicated side slot.
 #include <cstdio>
 
 #include "agg_internal.cuh"
@@ -73,6 +77,11 @@ __device__ __forceinline__ void set_status(Ctrl* c, agg_status s) {
   atomicOr(&c->status_bits, 1ull << (int)s);
 }
 
+// 4 bits of a byte-wise 0xFF/0x00 mask word, one per byte.
+__device__ __forceinline__ uint32_t byte_mask_bits(uint32_t m) {
+  return ((m >> 7) & 1u) | ((m >> 14) & 2u) | ((m >> 21) & 4u) | ((m >> 28) & 8u);
+}
+
 // ---------------------------------------------------------------- shared memory
 
 struct Smem {
@@ -86,10 +95,9 @@ struct Smem {
   unsigned long long scan_base;
   uint32_t warp_tot[WARPS];
   uint32_t scan_total;
-  uint32_t claims;
-  uint32_t full;
   uint32_t ok;
   uint32_t cache_used;
+  uint32_t first_spill;
 };
 
 struct Cache {
@@ -130,8 +138,8 @@ __device__ inline Cache carve_cache(unsigned char* base, uint32_t ns, bool mm) {
 
 // ---------------------------------------------------------------- grid barrier
 
-// Sense-counting grid barrier for a cooperative launch.  The wait is bounded:
-// after timeout_ns the block records AGG_ERR_TIMEOUT and returns false.
+// Counting grid barrier for a cooperative launch.  The wait is bounded: after
+// timeout_ns the block records AGG_ERR_TIMEOUT and returns false.
 __device__ bool grid_barrier(Ctrl* c, uint64_t timeout_ns, Smem& S) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -146,7 +154,7 @@ __device__ bool grid_barrier(Ctrl* c, uint64_t timeout_ns, Smem& S) {
     } else {
       const uint64_t t0 = globaltimer();
       while (ld_acquire_u32(&c->bar_gen) == g) {
-        __nanosleep(100);
+        __nanosleep(32);
         if (globaltimer() - t0 > timeout_ns) {
           set_status(c, AGG_ERR_TIMEOUT);
           ok = 0;
@@ -160,6 +168,21 @@ __device__ bool grid_barrier(Ctrl* c, uint64_t timeout_ns, Smem& S) {
   __syncthreads();
   return S.ok != 0;
 }
+
+// Phase timer of block 0 (diagnostics, reported by agg_get_stats).
+struct Timer {
+  uint64_t t;
+  __device__ void start() {
+    if (blockIdx.x == 0 && threadIdx.x == 0) t = globaltimer();
+  }
+  __device__ void lap(Ctrl* c, int phase) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const uint64_t now = globaltimer();
+      c->phase_ns[phase] += now - t;
+      t = now;
+    }
+  }
+};
 
 // ---------------------------------------------------------------- table access
 
@@ -181,6 +204,7 @@ struct Ent {
     }
   }
   __device__ static void reset(uint8_t* e) {
+    __stcg(reinterpret_cast<long long*>(e), (long long)EMPTY_KEY);
     __stcg(reinterpret_cast<unsigned long long*>(e + 8), 0ull);
     __stcg(reinterpret_cast<unsigned long long*>(e + 16), 0ull);
     if (ENT == ENT32_CSMM32) {
@@ -208,71 +232,47 @@ struct Ent {
   }
 };
 
-// Waits (bounded) until byte j of a tag word is no longer BUSY; returns the word.
-__device__ uint32_t wait_not_busy(const uint32_t* wp, uint32_t j, const HashParams& P) {
-  const uint64_t t0 = globaltimer();
-  uint32_t w;
-  while (true) {
-    w = ld_acquire_u32(wp);
-    if (((w >> (8 * j)) & 0xFFu) != TAG_BUSY) return w;
-    __nanosleep(20);
-    if (globaltimer() - t0 > P.timeout_ns) {
-      set_status(P.ctrl, AGG_ERR_TIMEOUT);
-      return w & ~(0xFFu << (8 * j)) | (TAG_CLOSED << (8 * j));  // give up: treat as closed
-    }
-  }
-}
-
-// Finds or claims the slot of `key`.  Returns the slot when the key is (now)
-// resident, -1 when the key must spill (chain closed, table full, or the probe
-// window holds only other keys).  *claimed is set when this call inserted it.
+// Finds or claims the slot of `key` in its window (buckets b0 and b0+1 of the
+// active table).  Returns the slot when the key is (now) resident, -1 when its
+// window holds only other keys (the key spills).  *claimed is set when this
+// call inserted the key.
 template <int ENT>
-__device__ long long probe_table(const HashParams& P, uint32_t s_act, long long key, uint64_t h, bool full,
-                                 uint32_t& claimed) {
-  uint32_t pos = (uint32_t)(((h >> 32) * (uint64_t)s_act) >> 32);
+__device__ long long probe_table(const HashParams& P, uint32_t s_act, long long key, uint64_t h, uint32_t& claimed) {
+  uint8_t* tag_bytes = reinterpret_cast<uint8_t*>(P.tags);
+  if (key == EMPTY_KEY) {  // the empty marker value itself: side slot, always resident
+    if (__ldcg(tag_bytes + P.slots) == 0) __stcg(tag_bytes + P.slots, (uint8_t)0x80);
+    return P.slots;
+  }
+  const uint32_t nb = s_act / BUCKET;
+  const uint32_t b0 = (uint32_t)(((h >> 32) * (uint64_t)nb) >> 32);
+  const uint32_t b1 = (b0 + 1 == nb) ? 0u : b0 + 1;
   const uint32_t tag = 0x80u | (uint32_t)(h & 0x7Fu);
-  uint32_t* tags = P.tags;
-  int steps = 0;
-  while (steps < MAX_PROBE) {
-    const uint32_t widx = pos >> 2;
-    uint32_t w = ld_acquire_u32(tags + widx);
-    for (uint32_t j = pos & 3u; j < 4 && steps < MAX_PROBE; ++j, ++steps) {
-      for (int attempt = 0;; ++attempt) {
-        const uint32_t b = (w >> (8 * j)) & 0xFFu;
-        const uint32_t slot = widx * 4 + j;
-        if (b == tag) {
-          const long long k2 = __ldcg(reinterpret_cast<const long long*>(Ent<ENT>::at(P.ent, slot)));
-          if (k2 == key) return slot;
-          break;
-        }
-        if (b >= 0x80u) break;
-        if (b == TAG_CLOSED) return -1;
-        if (b == TAG_BUSY) {
-          w = wait_not_busy(tags + widx, j, P);
-          continue;
-        }
-        // EMPTY: claim it for the key, or close the chain when the table is full.
-        const uint32_t nbyte = full ? TAG_CLOSED : TAG_BUSY;
-        const uint32_t nw = (w & ~(0xFFu << (8 * j))) | (nbyte << (8 * j));
-        const uint32_t old = atomicCAS(tags + widx, w, nw);
-        if (old != w) {
-          if (attempt > (1 << 16)) {
-            set_status(P.ctrl, AGG_ERR_TIMEOUT);
-            return -1;
-          }
-          w = ld_acquire_u32(tags + widx);
-          continue;
-        }
-        if (full) return -1;
-        __stcg(reinterpret_cast<long long*>(Ent<ENT>::at(P.ent, slot)), key);
-        __threadfence();
-        atomicXor(tags + widx, (TAG_BUSY ^ tag) << (8 * j));
-        claimed = 1;
-        return slot;
-      }
+  const uint32_t tag4 = tag * 0x01010101u;
+  const uint4 t0 = __ldcg(reinterpret_cast<const uint4*>(P.tags) + b0);
+  const uint4 t1 = __ldcg(reinterpret_cast<const uint4*>(P.tags) + b1);
+  const uint32_t w[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+  uint32_t cand = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint32_t m = __vcmpeq4(w[q], tag4) | __vcmpeq4(w[q], 0u);
+    cand |= byte_mask_bits(m) << (4 * q);
+  }
+  while (cand) {
+    const uint32_t i = __ffs(cand) - 1;
+    cand &= cand - 1;
+    const uint32_t slot = (i < BUCKET ? b0 : b1) * BUCKET + (i & (BUCKET - 1));
+    long long* kp = reinterpret_cast<long long*>(Ent<ENT>::at(P.ent, slot));
+    const long long k2 = __ldcg(kp);
+    if (k2 == key) return slot;
+    if (k2 != EMPTY_KEY) continue;
+    const long long old = (long long)atomicCAS(reinterpret_cast<unsigned long long*>(kp),
+                                               (unsigned long long)EMPTY_KEY, (unsigned long long)key);
+    if (old == EMPTY_KEY) {
+      __stcg(tag_bytes + slot, (uint8_t)tag);
+      claimed = 1;
+      return slot;
     }
-    pos = (widx + 1) * 4;
-    if (pos >= s_act) pos = 0;
+    if (old == key) return slot;
   }
   return -1;
 }
@@ -282,8 +282,7 @@ __device__ long long probe_table(const HashParams& P, uint32_t s_act, long long 
 struct Level {
   uint32_t level;
   uint64_t seed;
-  uint32_t s_act;     // active slots of this round
-  uint64_t cap;       // groups before the round's table counts as full
+  uint32_t s_act;     // active slots of this round (multiple of BUCKET)
   uint32_t dst;       // staging area receiving this level's spills
   uint32_t fan_mask;
 };
@@ -361,8 +360,6 @@ template <int ENT>
 __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const Cache& cc, long long (&k)[RPT],
                              long long (&v)[RPT], bool (&valid)[RPT], uint64_t tile_row0) {
   const uint32_t lane = threadIdx.x & 31;
-  const bool full = S.full != 0;
-  uint32_t my_claims = 0;
   bool sp[RPT];
   uint32_t part[RPT];
   bool any_sp = false;
@@ -400,10 +397,9 @@ __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const
     if (val && lane == leader) {
       if (!cache_hit<ENT>(cc, k[r], h, gc, gs, gmn, gmx)) {
         uint32_t claimed = 0;
-        const long long slot = probe_table<ENT>(P, L.s_act, k[r], h, full, claimed);
+        const long long slot = probe_table<ENT>(P, L.s_act, k[r], h, claimed);
         if (slot >= 0) {
           Ent<ENT>::add(Ent<ENT>::at(P.ent, (uint32_t)slot), P.ops, gc, gs, gmn, gmx);
-          my_claims += claimed;
           cache_insert(cc, S, k[r], h, (uint32_t)slot);
         } else {
           resident = false;
@@ -416,22 +412,10 @@ __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const
     any_sp |= sp[r];
   }
 
-  // ---- tile epilogue: publish claims, update the full flag
-  if (my_claims) atomicAdd(&S.claims, my_claims);
-  const int any = __syncthreads_or(any_sp);
-  if (threadIdx.x == 0) {
-    const uint32_t cl = S.claims;
-    S.claims = 0;
-    const unsigned long long occ =
-        cl ? atomicAdd(&P.ctrl->occupancy, (unsigned long long)cl) + cl : ld_relaxed_u64(&P.ctrl->occupancy);
-    if (!S.full && occ >= L.cap) {
-      S.full = 1;
-      if (L.level == 0) atomicMin(&P.ctrl->rows_at_full, (unsigned long long)tile_row0);
-    }
-  }
-  if (!any) {
-    __syncthreads();
-    return;
+  if (!__syncthreads_or(any_sp)) return;
+  if (threadIdx.x == 0 && L.level == 0 && S.first_spill) {
+    S.first_spill = 0;
+    atomicMin(&P.ctrl->rows_at_full, (unsigned long long)tile_row0);
   }
 
   // ---- spill: warp-aggregated ranks per partition
@@ -552,7 +536,25 @@ __device__ uint32_t block_exclusive_scan(uint32_t x, uint32_t& total, Smem& S) {
   return r;
 }
 
-// Writes every occupied slot of the active table to the output and resets it.
+template <int ENT>
+__device__ void emit_one(const HashParams& P, uint8_t* e, unsigned long long pos) {
+  long long key, mn, mx;
+  unsigned long long c, s;
+  Ent<ENT>::read(e, key, c, s, mn, mx);
+  if (pos < P.o_cap) {
+    P.o_keys[pos] = key;
+    if (P.o_count) P.o_count[pos] = c;
+    if (P.o_sum) P.o_sum[pos] = (long long)s;
+    if (P.o_min) P.o_min[pos] = mn;
+    if (P.o_max) P.o_max[pos] = mx;
+  } else {
+    set_status(P.ctrl, AGG_ERR_OUTPUT_CAPACITY);
+  }
+  Ent<ENT>::reset(e);
+}
+
+// Writes every occupied slot of the active table (and the side slot) to the
+// output and resets them.
 template <int ENT>
 __device__ void emit_table(const HashParams& P, uint32_t s_act, uint32_t level, Smem& S) {
   const uint32_t words = s_act / 4;
@@ -562,11 +564,18 @@ __device__ void emit_table(const HashParams& P, uint32_t s_act, uint32_t level, 
     const uint32_t w0 = seg * seg_words + threadIdx.x * WPT;
     uint32_t tw[WPT];
     uint32_t oc = 0;
+    if (w0 + WPT <= words) {
+      const uint4 t = __ldcg(reinterpret_cast<const uint4*>(P.tags + w0));
+      tw[0] = t.x;
+      tw[1] = t.y;
+      tw[2] = t.z;
+      tw[3] = t.w;
+    } else {
 #pragma unroll
-    for (uint32_t q = 0; q < WPT; ++q) {
-      tw[q] = (w0 + q < words) ? __ldcg(P.tags + w0 + q) : 0u;
-      oc += __popc(tw[q] & 0x80808080u);
+      for (uint32_t q = 0; q < WPT; ++q) tw[q] = (w0 + q < words) ? __ldcg(P.tags + w0 + q) : 0u;
     }
+#pragma unroll
+    for (uint32_t q = 0; q < WPT; ++q) oc += __popc(tw[q] & 0x80808080u);
     uint32_t total;
     const uint32_t off = block_exclusive_scan(oc, total, S);
     if (threadIdx.x == 0) {
@@ -580,27 +589,24 @@ __device__ void emit_table(const HashParams& P, uint32_t s_act, uint32_t level, 
       if (tw[q] == 0) continue;
 #pragma unroll
       for (uint32_t j = 0; j < 4; ++j) {
-        const uint32_t b = (tw[q] >> (8 * j)) & 0xFFu;
-        if (b < 0x80u) continue;
-        uint8_t* e = Ent<ENT>::at(P.ent, (w0 + q) * 4 + j);
-        long long key, mn, mx;
-        unsigned long long c, s;
-        Ent<ENT>::read(e, key, c, s, mn, mx);
-        if (pos < P.o_cap) {
-          P.o_keys[pos] = key;
-          if (P.o_count) P.o_count[pos] = c;
-          if (P.o_sum) P.o_sum[pos] = (long long)s;
-          if (P.o_min) P.o_min[pos] = mn;
-          if (P.o_max) P.o_max[pos] = mx;
-        } else {
-          set_status(P.ctrl, AGG_ERR_OUTPUT_CAPACITY);
-        }
+        if (((tw[q] >> (8 * j)) & 0x80u) == 0) continue;
+        emit_one<ENT>(P, Ent<ENT>::at(P.ent, (w0 + q) * 4 + j), pos);
         ++pos;
-        Ent<ENT>::reset(e);
       }
       __stcg(P.tags + w0 + q, 0u);
     }
     __syncthreads();
+  }
+  // the side slot of the empty-marker key
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    uint8_t* tb = reinterpret_cast<uint8_t*>(P.tags) + P.slots;
+    if (__ldcg(tb)) {
+      const unsigned long long pos = atomicAdd(&P.ctrl->out_count, 1ull);
+      atomicAdd(&P.ctrl->resident_groups[level], 1ull);
+      emit_one<ENT>(P, Ent<ENT>::at(P.ent, P.slots), pos);
+      __stcg(reinterpret_cast<long long*>(Ent<ENT>::at(P.ent, P.slots)), (long long)EMPTY_KEY);
+      __stcg(tb, (uint8_t)0);
+    }
   }
 }
 
@@ -628,6 +634,10 @@ __device__ void final_step(const HashParams& P, uint32_t levels) {
     C->spill_records[l] = 0;
     C->resident_groups[l] = 0;
   }
+  for (int ph = 0; ph < PHASES; ++ph) {
+    C->last_phase_ns[ph] = V->phase_ns[ph];
+    C->phase_ns[ph] = 0;
+  }
   C->occupancy = 0;
   C->out_count = 0;
   C->pool_next[0] = 0;
@@ -644,6 +654,9 @@ __device__ void final_step(const HashParams& P, uint32_t levels) {
   C->done_count = 0;
 }
 
+// Phase indices of Ctrl::phase_ns (block 0's view).
+enum Phase { PH_L0 = 0, PH_L0_WAIT, PH_L0_EMIT, PH_LISTS, PH_ROUND_AGG, PH_ROUND_WAIT, PH_ROUND_EMIT, PH_TOTAL };
+
 // ---------------------------------------------------------------- the kernel
 
 template <int ENT, int VT>
@@ -653,6 +666,9 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
   const Cache cc = carve_cache(smem_raw + ((sizeof(Smem) + 15) & ~size_t(15)), P.ns, Ent<ENT>::MM);
   Ctrl* C = P.ctrl;
   const uint32_t fan = 1u << P.fan_log2;
+  Timer tm, total;
+  tm.start();
+  total.start();
 
   for (uint32_t p = threadIdx.x; p < MAX_FAN; p += THREADS) {
     S.cnt[p] = 0;
@@ -670,10 +686,9 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
     }
   }
   if (threadIdx.x == 0) {
-    S.claims = 0;
-    S.full = 0;
     S.cache_used = 0;
     S.spilled = 0;
+    S.first_spill = 1;
   }
   __syncthreads();
 
@@ -683,7 +698,6 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
     L.level = 0;
     L.seed = level_seed(P.seed, 0);
     L.s_act = P.s_act0;
-    L.cap = (uint64_t)(P.lf * (double)P.s_act0);
     L.dst = 0;
     L.fan_mask = fan - 1;
     const uint64_t ntiles = (P.n + TILE - 1) / TILE;
@@ -730,15 +744,19 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
     }
     cache_flush<ENT>(P, cc, S);
     finalize_chunks(P, S, 0, 0);
+    tm.lap(C, PH_L0);
     if (!grid_barrier(C, P.timeout_ns, S)) return;
+    tm.lap(C, PH_L0_WAIT);
     const unsigned long long spilled = ld_relaxed_u64(&C->pool_next[0]);
     emit_table<ENT>(P, L.s_act, 0, S);
-    if (threadIdx.x == 0 && blockIdx.x == 0) C->occupancy = 0;
+    tm.lap(C, PH_L0_EMIT);
     if (spilled == 0) {
+      total.lap(C, PH_TOTAL);
       final_step(P, 1);
       return;
     }
     if (!grid_barrier(C, P.timeout_ns, S)) return;
+    tm.lap(C, PH_ROUND_WAIT);
   }
 
   // ================= levels 1..: recursive processing of spilled partitions
@@ -799,6 +817,7 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
         C->part_cursor[set ^ 1][p] = 0;
       }
     }
+    tm.lap(C, PH_LISTS);
     // Rounds: consecutive partitions packed while their records fit the table.
     const uint64_t cap_full = (uint64_t)(P.lf * (double)P.slots);
     uint32_t p = 0;
@@ -816,16 +835,13 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
       Level L;
       L.level = level;
       L.seed = level_seed(P.seed, level);
-      uint64_t want = (uint64_t)((double)tot / P.lf) + 4;
-      want = (want + 3) & ~3ull;
+      uint64_t want = (uint64_t)((double)tot / P.lf) + BUCKET;
+      want = (want + BUCKET - 1) / BUCKET * BUCKET;
       if (want < MIN_SLOTS) want = MIN_SLOTS;
       if (want > P.slots) want = P.slots;
       L.s_act = (uint32_t)want;
-      L.cap = (uint64_t)(P.lf * (double)L.s_act);
       L.dst = dst;
       L.fan_mask = fan - 1;
-      if (threadIdx.x == 0) S.full = 0;
-      __syncthreads();
       const uint32_t c0 = S.begin[p], c1 = S.begin[q];
       const uint64_t nrec_slots = (uint64_t)(c1 - c0) * CH;
       const uint64_t ntiles = (nrec_slots + TILE - 1) / TILE;
@@ -854,18 +870,21 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
         process_rows<ENT>(P, L, S, cc, k, v, valid, 0);
       }
       cache_flush<ENT>(P, cc, S);
+      tm.lap(C, PH_ROUND_AGG);
       if (!grid_barrier(C, P.timeout_ns, S)) return;
+      tm.lap(C, PH_ROUND_WAIT);
       emit_table<ENT>(P, L.s_act, level, S);
-      if (threadIdx.x == 0 && blockIdx.x == 0) {
-        C->occupancy = 0;
-        C->rounds += 1;
-      }
+      if (threadIdx.x == 0 && blockIdx.x == 0) C->rounds += 1;
+      tm.lap(C, PH_ROUND_EMIT);
       if (!grid_barrier(C, P.timeout_ns, S)) return;
+      tm.lap(C, PH_ROUND_WAIT);
       p = q;
     }
     finalize_chunks(P, S, dst, level);
     if (!grid_barrier(C, P.timeout_ns, S)) return;
+    tm.lap(C, PH_ROUND_WAIT);
     if (ld_relaxed_u64(&C->pool_next[dst]) == 0) {
+      total.lap(C, PH_TOTAL);
       final_step(P, level + 1);
       return;
     }
@@ -874,12 +893,13 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
 
 template <int ENT>
 __global__ void init_table_kernel(uint8_t* ent, uint32_t* tags, uint32_t slots) {
-  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < slots; s += (uint64_t)gridDim.x * blockDim.x) {
-    uint8_t* e = Ent<ENT>::at(ent, (uint32_t)s);
-    *reinterpret_cast<long long*>(e) = 0;
-    Ent<ENT>::reset(e);
-    if ((s & 3) == 0) tags[s >> 2] = 0;
+  // slots + 1 entries (the last is the side slot) and slots + BUCKET tag bytes
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s <= slots; s += (uint64_t)gridDim.x * blockDim.x) {
+    Ent<ENT>::reset(Ent<ENT>::at(ent, (uint32_t)s));
   }
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < (slots + BUCKET) / 4;
+       w += (uint64_t)gridDim.x * blockDim.x)
+    tags[w] = 0;
 }
 
 template <int ENT, int VT>
@@ -926,7 +946,7 @@ cudaError_t hash_launch(int ent_kind, int vt, const HashParams& p, const KernelI
 }
 
 cudaError_t hash_init_table(uint8_t* ent, uint32_t* tags, uint32_t slots, int ent_kind, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((slots + 255) / 256 > 4096 ? 4096 : (slots + 255) / 256);
+  const unsigned blocks = (unsigned)((slots + 255) / 256 > 4096 ? 4096 : (slots + 255) / 256 + 1);
   if (ent_kind == ENT32_CS) init_table_kernel<ENT32_CS><<<blocks, 256, 0, s>>>(ent, tags, slots);
   else if (ent_kind == ENT32_CSMM32) init_table_kernel<ENT32_CSMM32><<<blocks, 256, 0, s>>>(ent, tags, slots);
   else init_table_kernel<ENT64><<<blocks, 256, 0, s>>>(ent, tags, slots);

@@ -11,8 +11,13 @@ struct SortState {
   void* work = nullptr;      // double buffers + histograms (inside the budget)
   uint64_t work_bytes = 0;
   uint64_t reserved_rows = 0;
+  uint64_t round_rows = 0;   // records sorted per round (fits the budget)
+  uint32_t epoch = 0;        // look-back status epoch, one per pass
   uint64_t last_buckets = 0;
   uint64_t last_passes = 0;
+  uint64_t last_rounds = 0;
+  uint64_t last_levels = 0;
+  uint64_t launches = 0;
 };
 
 agg_status sort_reserve(SortState& s, uint64_t rows, size_t budget, const agg_spec& spec);
@@ -21,5 +26,6 @@ agg_status sort_run(SortState& s, size_t budget, const agg_spec& spec, Ctrl* ctr
 void sort_free(SortState& s);
 uint64_t sort_staging_bytes(const SortState& s);
 void sort_fill_stats(const SortState& s, agg_stats* st);
+inline uint64_t sort_launches(const SortState& s) { return s.launches; }
 
 }  // namespace agg
