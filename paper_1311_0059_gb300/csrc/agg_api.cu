@@ -329,7 +329,7 @@ agg_status agg_create(size_t budget, const agg_spec* spec, agg_handle** out) {
     agg_destroy(h);
     return AGG_ERR_OOM;
   }
-  if (hash_kernel_info(h->ent_kind, spec->value_type, h->tune.smem_entries > 1 ? h->tune.smem_entries : 0,
+  if (hash_kernel_info(h->ent_kind, spec->value_type, h->tune.smem_entries > 1 ? h->tune.smem_entries : DEFAULT_NS,
                        h->device, &h->ki) != cudaSuccess) {
     cudaGetLastError();
     agg_destroy(h);
@@ -353,8 +353,8 @@ agg_status agg_set_tuning(agg_handle* h, const agg_tuning* t) {
     return AGG_OK;
   }
   KernelInfo ki;
-  if (hash_kernel_info(h->ent_kind, h->spec.value_type, e.smem_entries > 1 ? e.smem_entries : 0, h->device, &ki) !=
-      cudaSuccess) {
+  if (hash_kernel_info(h->ent_kind, h->spec.value_type, e.smem_entries > 1 ? e.smem_entries : DEFAULT_NS, h->device,
+                       &ki) != cudaSuccess) {
     cudaGetLastError();
     return AGG_ERR_CUDA;
   }
@@ -456,7 +456,8 @@ agg_status agg_run(agg_handle* h, const int64_t* d_keys, const void* d_vals, uin
   p.fan_log2 = log2u(fan);
   p.lf = h->tune.max_load_factor;
   p.s_act0 = active_slots(h->spec.expected_groups ? h->spec.expected_groups : (n ? n : 1), p.lf, h->slots);
-  p.ns = h->tune.smem_entries > 1 ? h->tune.smem_entries : 0;
+  p.ns = h->tune.smem_entries > 1 ? h->tune.smem_entries : DEFAULT_NS;
+  p.cache = h->tune.smem_entries != 1;
   p.dedup = h->tune.warp_dedup == 1 ? 1 : 0;
   p.timeout_ns = TIMEOUT_NS;
   if (hash_launch(h->ent_kind, h->spec.value_type, p, h->ki, s) != cudaSuccess) {
@@ -485,10 +486,12 @@ agg_status agg_sync(agg_handle* h, uint64_t* n_groups_host) {
   if (n_groups_host) *n_groups_host = ng;
   const agg_status st = status_from_bits(bits);
   if (bits) {
-    if (bits & (1ull << (int)AGG_ERR_TIMEOUT)) {
-      // a timed-out wait leaves barrier state behind: rebuild the working memory
+    if (bits & ~(1ull << (int)AGG_ERR_OUTPUT_CAPACITY)) {
+      // an aborted or inconsistent run may leave barrier or round state behind:
+      // rebuild the working memory
       cudaDeviceSynchronize();
-      agg_status r = reinit_working(h, nullptr);
+      agg_status r = h->spec.path == AGG_PATH_SORT ? AGG_OK : reinit_working(h, nullptr);
+      if (h->spec.path == AGG_PATH_SORT) cudaMemset(h->ctrl, 0, sizeof(Ctrl));
       if (r != AGG_OK) return r;
     } else {
       unsigned long long zero = 0;

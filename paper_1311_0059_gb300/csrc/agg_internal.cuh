@@ -15,16 +15,18 @@ constexpr int RPT = 4;                     // rows per thread per tile
 constexpr int TILE = THREADS * RPT;        // rows per block tile
 constexpr uint32_t CH = 2048;              // records per staging chunk (32 KiB)
 constexpr int MAX_FAN = 256;               // largest spill fan-out
-constexpr uint32_t BUCKET = 16;            // slots per bucket: one 16-byte load of tag bytes
+constexpr uint32_t BUCKET = 32;            // slots per bucket: one 32-byte sector of tag bytes
 constexpr uint32_t MIN_SLOTS = 4096;       // smallest active table of a round
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr int64_t EMPTY_KEY = INT64_MIN;   // empty key slot; this one key value lives in a side slot
 constexpr int64_t SKEY_EMPTY = INT64_MIN;  // empty marker of the shared-memory cache
 constexpr int PHASES = 8;                  // phase timers kept by block 0
+constexpr uint32_t NSUB_MAX = 4096;        // sub-partitions of one shared-memory round
+constexpr uint64_t ROUND_CAP_MAX = 4ull << 20;  // records of one shared-memory round (L2-sized)
 constexpr uint64_t REC_BYTES = 16;         // spilled record: (int64 key, int64 value)
 // One tile adds at most TILE rows to a partition, so at most one new chunk is
 // opened per partition per tile.
-static_assert(TILE <= (int)CH, "a tile must fit in one staging chunk");
+static_assert(TILE == (int)CH, "a tile is one staging chunk");
 
 // Table entry layouts (bytes): key, count, sum, then MIN/MAX when requested.
 enum EntKind { ENT32_CS = 0, ENT32_CSMM32 = 1, ENT64 = 2 };
@@ -53,6 +55,13 @@ struct alignas(128) Ctrl {
   unsigned long long part_records[2][MAX_FAN];
   unsigned int part_chunks[2][MAX_FAN];
   unsigned int part_cursor[2][MAX_FAN];
+  // shared-memory rounds of levels >= 1 (two sets by round parity)
+  unsigned int sub_tot[2][NSUB_MAX];
+  unsigned int sub_cur[2][NSUB_MAX];
+  unsigned int sub_base[2][NSUB_MAX + 1];
+  unsigned long long lvl_sub_records[2];  // records aggregated in shared memory (by round parity)
+  unsigned long long lvl_sub_groups[2];   // groups they formed (keys-per-record estimate)
+  unsigned int overflow_used[2];          // a key of the level (by parity) went to the global table
   // ---- snapshot of the last completed run
   unsigned long long last_n_rows;
   unsigned long long last_n_groups;
@@ -92,9 +101,9 @@ struct HashParams {
   uint32_t fan_log2;
   double lf;           // maximum load factor
   uint32_t s_act0;     // active slots at level 0
-  uint32_t ns;         // shared-memory cache entries (power of two) or 0
+  uint32_t ns;         // shared-memory table entries (power of two)
   uint32_t dedup;      // warp-level key dedup on/off
-  uint32_t pad;
+  uint32_t cache;      // shared-memory cache of resident groups on/off
   uint64_t timeout_ns; // bounded waits give up after this long
 };
 

@@ -15,16 +15,16 @@
 // packed into one table round (partition tuning, Section 4.3.3).  Phases are
 // separated by grid barriers whose waits are bounded.
 //
-// Table and residency.  Slots form buckets of 16; a key may live only in the
-// 32 slots of its two consecutive buckets (its window), filled in order.  A key
-// slot changes once per round, from EMPTY to a key, by a 64-bit atomicCAS, so
-// "k is absent and its window holds only other keys" can never become false
-// later in the round: such a key spills consistently, and a key is never both
-// resident and spilled.  "Full" (Section 3.2: no new group fits) is therefore
-// judged per window.  A tag byte per slot (0x80 | 7 hash bits, written after the
-// claim) is a compact filter kept in L2: probes compare 32 tags at once and
-// read keys only where a tag matches or is still zero.  The key value that
-// marks an empty slot (INT64_MIN) is kept in a dedicated side slot.
+// Table and residency.  Slots form buckets of 32; a key may live only in its
+// hash bucket, in the first slot that was free when it arrived.  A key slot
+// changes once per round, from EMPTY to a key, by a 64-bit atomicCAS, so "k is
+// absent and its bucket holds 32 other keys" can never become false later in
+// the round: such a key spills consistently, and a key is never both resident
+// and spilled.  "Full" (Section 3.2: no new group fits) is therefore judged per
+// bucket.  A tag byte per slot (0x80 | 7 hash bits, written after the claim) is
+// a compact filter kept in L2: a probe reads its bucket's 32 tags in one 32-byte
+// sector and reads keys only where a tag matches or is still zero.  The key
+// value that marks an empty slot (INT64_MIN) is kept in a dedicated side slot.
 #include <cstdio>
 
 #include "agg_internal.cuh"
@@ -73,6 +73,11 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// Asks the memory system to stage [p, p + bytes) in L2 (p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  if (bytes >= 16) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes & ~15u) : "memory");
+}
+
 __device__ __forceinline__ void set_status(Ctrl* c, agg_status s) {
   atomicOr(&c->status_bits, 1ull << (int)s);
 }
@@ -98,6 +103,10 @@ struct Smem {
   uint32_t ok;
   uint32_t cache_used;
   uint32_t first_spill;
+  uint32_t tiles;      // tiles processed by this block (adaptive sampling clock)
+  uint32_t use_cache;
+  uint32_t use_dedup;
+  uint32_t st_rows, st_hits, st_dups;
 };
 
 struct Cache {
@@ -232,35 +241,49 @@ struct Ent {
   }
 };
 
-// Finds or claims the slot of `key` in its window (buckets b0 and b0+1 of the
-// active table).  Returns the slot when the key is (now) resident, -1 when its
-// window holds only other keys (the key spills).  *claimed is set when this
-// call inserted the key.
-template <int ENT>
-__device__ long long probe_table(const HashParams& P, uint32_t s_act, long long key, uint64_t h, uint32_t& claimed) {
-  uint8_t* tag_bytes = reinterpret_cast<uint8_t*>(P.tags);
-  if (key == EMPTY_KEY) {  // the empty marker value itself: side slot, always resident
-    if (__ldcg(tag_bytes + P.slots) == 0) __stcg(tag_bytes + P.slots, (uint8_t)0x80);
-    return P.slots;
-  }
-  const uint32_t nb = s_act / BUCKET;
-  const uint32_t b0 = (uint32_t)(((h >> 32) * (uint64_t)nb) >> 32);
-  const uint32_t b1 = (b0 + 1 == nb) ? 0u : b0 + 1;
-  const uint32_t tag = 0x80u | (uint32_t)(h & 0x7Fu);
-  const uint32_t tag4 = tag * 0x01010101u;
-  const uint4 t0 = __ldcg(reinterpret_cast<const uint4*>(P.tags) + b0);
-  const uint4 t1 = __ldcg(reinterpret_cast<const uint4*>(P.tags) + b1);
-  const uint32_t w[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+// Candidate slots of a bucket, in probe order: tag byte equal to the key's tag,
+// or still zero (free, or claimed a moment ago with its tag not yet written).
+// The bucket's 32 tag bytes are one 32-byte sector, read with one 256-bit load.
+__device__ __forceinline__ uint32_t bucket_candidates(const HashParams& P, uint32_t b, uint32_t tag4) {
+  unsigned long long q0, q1, q2, q3;
+  asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
+               : "=l"(q0), "=l"(q1), "=l"(q2), "=l"(q3)
+               : "l"(reinterpret_cast<const uint8_t*>(P.tags) + (size_t)b * BUCKET));
+  const unsigned long long q[4] = {q0, q1, q2, q3};
   uint32_t cand = 0;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const uint32_t m = __vcmpeq4(w[q], tag4) | __vcmpeq4(w[q], 0u);
-    cand |= byte_mask_bits(m) << (4 * q);
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t lo = (uint32_t)q[i], hi = (uint32_t)(q[i] >> 32);
+    cand |= byte_mask_bits(__vcmpeq4(lo, tag4) | __vcmpeq4(lo, 0u)) << (8 * i);
+    cand |= byte_mask_bits(__vcmpeq4(hi, tag4) | __vcmpeq4(hi, 0u)) << (8 * i + 4);
+  }
+  return cand;
+}
+
+__device__ __forceinline__ uint32_t home_bucket(uint64_t h, uint32_t s_act) {
+  return (uint32_t)(((h >> 32) * (uint64_t)(s_act / BUCKET)) >> 32);
+}
+
+__device__ __forceinline__ uint32_t key_tag(uint64_t h) { return 0x80u | (uint32_t)(h & 0x7Fu); }
+
+// Finds or claims the slot of `key` in its bucket, given the bucket's candidate
+// mask.  A key may live only in its bucket, in the first slot that was free
+// when it arrived: the candidates are visited in slot order; a free slot is
+// claimed by a 64-bit CAS; a slot taken meanwhile by another key is passed.
+// Returns the slot when the key is (now) resident, -1 when the bucket holds 32
+// other keys (the key spills).  *claimed is set when this call inserted it.
+template <int ENT>
+__device__ long long probe_table(const HashParams& P, uint32_t b, uint32_t cand, long long key, uint32_t tag,
+                                 uint32_t& claimed) {
+  if (key == EMPTY_KEY) {  // the empty marker value itself: side slot, always resident
+    uint8_t* tb = reinterpret_cast<uint8_t*>(P.tags) + P.slots;
+    if (__ldcg(tb) == 0) __stcg(tb, (uint8_t)0x80);
+    return P.slots;
   }
   while (cand) {
     const uint32_t i = __ffs(cand) - 1;
     cand &= cand - 1;
-    const uint32_t slot = (i < BUCKET ? b0 : b1) * BUCKET + (i & (BUCKET - 1));
+    const uint32_t slot = b * BUCKET + i;
     long long* kp = reinterpret_cast<long long*>(Ent<ENT>::at(P.ent, slot));
     const long long k2 = __ldcg(kp);
     if (k2 == key) return slot;
@@ -268,7 +291,7 @@ __device__ long long probe_table(const HashParams& P, uint32_t s_act, long long 
     const long long old = (long long)atomicCAS(reinterpret_cast<unsigned long long*>(kp),
                                                (unsigned long long)EMPTY_KEY, (unsigned long long)key);
     if (old == EMPTY_KEY) {
-      __stcg(tag_bytes + slot, (uint8_t)tag);
+      __stcg(reinterpret_cast<uint8_t*>(P.tags) + slot, (uint8_t)tag);
       claimed = 1;
       return slot;
     }
@@ -354,62 +377,153 @@ __device__ void cache_flush(const HashParams& P, const Cache& cc, Smem& S) {
 
 // ---------------------------------------------------------------- one tile of rows
 
+// Per-block adaptive features: every SAMPLE_PERIOD tiles, SAMPLE_TILES tiles
+// run with warp dedup and the shared-memory cache both on and count how many
+// rows each saves; the block keeps a feature on while it pays.
+constexpr uint32_t SAMPLE_PERIOD = 32, SAMPLE_TILES = 2;
+
+__device__ __forceinline__ void adapt_begin_tile(Smem& S, bool cache_allowed, bool dedup_allowed) {
+  if (threadIdx.x == 0) {
+    const bool sampling = (S.tiles % SAMPLE_PERIOD) < SAMPLE_TILES;
+    if (sampling) {
+      S.use_cache = cache_allowed;
+      S.use_dedup = dedup_allowed;
+    }
+  }
+}
+
+__device__ __forceinline__ void adapt_end_tile(Smem& S, bool cache_allowed, bool dedup_allowed) {
+  if (threadIdx.x == 0) {
+    const uint32_t ph = S.tiles % SAMPLE_PERIOD;
+    if (ph == SAMPLE_TILES - 1) {
+      const uint32_t rows = S.st_rows ? S.st_rows : 1;
+      S.use_cache = cache_allowed && S.st_hits * 20u >= rows;   // >= 5% of rows absorbed
+      S.use_dedup = dedup_allowed && S.st_dups * 50u >= rows;   // >= 2% of rows combined
+      S.st_rows = S.st_hits = S.st_dups = 0;
+    }
+    S.tiles += 1;
+  }
+}
+
+template <int ENT>
+__device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, const Cache& cc, long long (&k)[RPT],
+                                 long long (&v)[RPT], const bool (&need)[RPT], uint64_t tile_row0, bool cache_ins);
+
 // Aggregates up to RPT rows per thread (block-uniform call), then spills the
 // rows whose keys are not resident.  `tile_row0` orders level-0 tiles.
 template <int ENT>
 __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const Cache& cc, long long (&k)[RPT],
                              long long (&v)[RPT], bool (&valid)[RPT], uint64_t tile_row0) {
   const uint32_t lane = threadIdx.x & 31;
-  bool sp[RPT];
-  uint32_t part[RPT];
-  bool any_sp = false;
+  const bool use_cache = S.use_cache && cc.n;
+  const bool use_dedup = S.use_dedup;
+  const bool sampling = (S.tiles % SAMPLE_PERIOD) < SAMPLE_TILES;
+  bool need[RPT];
+  uint32_t hits = 0, dups = 0;
 
+  // ---- shared-memory cache of resident groups (with warp dedup of equal keys)
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) need[r] = valid[r];
+  if (use_cache) {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const bool val = valid[r];
+      const uint64_t h = fmix64((uint64_t)k[r] ^ L.seed);
+      uint32_t peers = 1u << lane, leader = lane;
+      unsigned long long gc = 1, gs = (unsigned long long)v[r];
+      long long gmn = v[r], gmx = v[r];
+      if (use_dedup) {
+        const uint32_t vm = __ballot_sync(FULL_MASK, val);
+        if (val) peers = __match_any_sync(vm, k[r]);
+        leader = __ffs(peers) - 1;
+        const uint32_t gsize = __popc(peers);
+        const uint32_t maxg = __reduce_max_sync(FULL_MASK, gsize);
+        if (maxg > 1) {
+          uint32_t rem = (val && lane == leader) ? (peers & ~(1u << lane)) : 0u;
+          for (uint32_t it = 1; it < maxg; ++it) {
+            const int src = rem ? __ffs(rem) - 1 : (int)lane;
+            rem &= rem - 1;
+            const long long ov = __shfl_sync(FULL_MASK, v[r], src);
+            if (src != (int)lane) {
+              gs += (unsigned long long)ov;
+              gmn = ov < gmn ? ov : gmn;
+              gmx = ov > gmx ? ov : gmx;
+            }
+          }
+          gc = gsize;
+        }
+        if (val && lane == leader) dups += gsize - 1;
+      }
+      bool hit = false;
+      if (val && lane == leader) {
+        hit = cache_hit<ENT>(cc, k[r], h, gc, gs, gmn, gmx);
+        hits += hit ? (uint32_t)gc : 0u;
+      }
+      if (use_dedup) hit = __shfl_sync(FULL_MASK, hit, leader);
+      need[r] = val && !hit;
+    }
+  } else if (sampling && use_dedup) {
+    // no cache: dedup only measured (global updates stay per row)
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const uint32_t vm = __ballot_sync(FULL_MASK, valid[r]);
+      if (valid[r]) {
+        const uint32_t peers = __match_any_sync(vm, k[r]);
+        if ((int)lane == __ffs(peers) - 1) dups += __popc(peers) - 1;
+      }
+    }
+  }
+
+  if (sampling) {
+    uint32_t nv = 0;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) nv += valid[r];
+    const uint32_t a = __reduce_add_sync(FULL_MASK, nv), b = __reduce_add_sync(FULL_MASK, hits),
+                   c = __reduce_add_sync(FULL_MASK, dups);
+    if (lane == 0) {
+      atomicAdd(&S.st_rows, a);
+      atomicAdd(&S.st_hits, b);
+      atomicAdd(&S.st_dups, c);
+    }
+  }
+
+  global_and_spill<ENT>(P, L, S, cc, k, v, need, tile_row0, use_cache || sampling);
+}
+
+// Updates the global table for every row with need[r] set (claiming slots for
+// new keys), then spills the rows whose keys are not resident to the next
+// level's partitions.  Block-uniform call.  `cache_ins` records newly found
+// slots in the shared-memory cache.
+template <int ENT>
+__device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, const Cache& cc, long long (&k)[RPT],
+                                 long long (&v)[RPT], const bool (&need)[RPT], uint64_t tile_row0, bool cache_ins) {
+  const uint32_t lane = threadIdx.x & 31;
+  // ---- global table: bucket tags of every remaining row first, then resolve
+  uint32_t cand[RPT];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    const bool val = valid[r];
+    cand[r] = 0;
+    if (need[r] && k[r] != EMPTY_KEY) {
+      const uint64_t h = fmix64((uint64_t)k[r] ^ L.seed);
+      cand[r] = bucket_candidates(P, home_bucket(h, L.s_act), key_tag(h) * 0x01010101u);
+    }
+  }
+  bool sp[RPT];
+  bool any_sp = false;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    sp[r] = false;
+    if (!need[r]) continue;
     const uint64_t h = fmix64((uint64_t)k[r] ^ L.seed);
-    uint32_t peers = 1u << lane;
-    uint32_t leader = lane;
-    unsigned long long gc = 1, gs = (unsigned long long)v[r];
-    long long gmn = v[r], gmx = v[r];
-    if (P.dedup) {
-      const uint32_t vm = __ballot_sync(FULL_MASK, val);
-      if (val) peers = __match_any_sync(vm, k[r]);
-      leader = __ffs(peers) - 1;
-      const uint32_t gsize = __popc(peers);
-      const uint32_t maxg = __reduce_max_sync(FULL_MASK, gsize);
-      if (maxg > 1) {
-        uint32_t rem = (val && lane == leader) ? (peers & ~(1u << lane)) : 0u;
-        for (uint32_t it = 1; it < maxg; ++it) {
-          const int src = rem ? __ffs(rem) - 1 : (int)lane;
-          rem &= rem - 1;
-          const long long ov = __shfl_sync(FULL_MASK, v[r], src);
-          if (src != (int)lane) {
-            gs += (unsigned long long)ov;
-            gmn = ov < gmn ? ov : gmn;
-            gmx = ov > gmx ? ov : gmx;
-          }
-        }
-        gc = gsize;
-      }
+    uint32_t claimed = 0;
+    const long long slot = probe_table<ENT>(P, home_bucket(h, L.s_act), cand[r], k[r], key_tag(h), claimed);
+    if (slot >= 0) {
+      Ent<ENT>::add(Ent<ENT>::at(P.ent, (uint32_t)slot), P.ops, 1ull, (unsigned long long)v[r], v[r], v[r]);
+      if (cache_ins) cache_insert(cc, S, k[r], h, (uint32_t)slot);
+    } else {
+      sp[r] = true;
+      any_sp = true;
     }
-    bool resident = true;
-    if (val && lane == leader) {
-      if (!cache_hit<ENT>(cc, k[r], h, gc, gs, gmn, gmx)) {
-        uint32_t claimed = 0;
-        const long long slot = probe_table<ENT>(P, L.s_act, k[r], h, claimed);
-        if (slot >= 0) {
-          Ent<ENT>::add(Ent<ENT>::at(P.ent, (uint32_t)slot), P.ops, gc, gs, gmn, gmx);
-          cache_insert(cc, S, k[r], h, (uint32_t)slot);
-        } else {
-          resident = false;
-        }
-      }
-    }
-    if (P.dedup) resident = __shfl_sync(FULL_MASK, resident, leader);
-    sp[r] = val && !resident;
-    part[r] = (uint32_t)(h >> 8) & L.fan_mask;
-    any_sp |= sp[r];
   }
 
   if (!__syncthreads_or(any_sp)) return;
@@ -419,9 +533,10 @@ __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const
   }
 
   // ---- spill: warp-aggregated ranks per partition
-  uint32_t rank[RPT];
+  uint32_t part[RPT], rank[RPT];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
+    part[r] = (uint32_t)(fmix64((uint64_t)k[r] ^ L.seed) >> 8) & L.fan_mask;
     const uint32_t vm = __ballot_sync(FULL_MASK, sp[r]);
     rank[r] = 0;
     if (sp[r]) {
@@ -610,6 +725,282 @@ __device__ void emit_table(const HashParams& P, uint32_t s_act, uint32_t level, 
   }
 }
 
+
+// ---------------------------------------------------------------- shared-memory rounds
+
+// Aggregates one record into the block's shared-memory sub-partition table.
+// A key may occupy only the first free slot of its 16-slot probe window, and
+// slots are not freed while the sub-partition is processed, so a key that finds
+// its window full of other keys never enters the table later: all of its rows
+// overflow consistently (to the global table).  Returns false on overflow.
+template <int ENT>
+__device__ __forceinline__ bool sub_upsert(const Cache& cc, long long key, uint64_t h, long long v) {
+  if (key == SKEY_EMPTY) return false;
+  uint32_t idx = (uint32_t)(h >> 32) & (cc.n - 1);
+#pragma unroll 1
+  for (int i = 0; i < 16; ++i) {
+    long long kk = *reinterpret_cast<volatile long long*>(cc.key + idx);
+    if (kk == SKEY_EMPTY) {
+      kk = (long long)atomicCAS(reinterpret_cast<unsigned long long*>(cc.key + idx), (unsigned long long)SKEY_EMPTY,
+                                (unsigned long long)key);
+      if (kk == SKEY_EMPTY) kk = key;
+    }
+    if (kk == key) {
+      atomicAdd(cc.cnt + idx, 1ull);
+      atomicAdd(cc.sum + idx, (unsigned long long)v);
+      if (Ent<ENT>::MM) {
+        atomicMin(cc.mn + idx, v);
+        atomicMax(cc.mx + idx, v);
+      }
+      return true;
+    }
+    idx = (idx + 1) & (cc.n - 1);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void cache_reset_all(const Cache& cc, Smem& S, bool mm) {
+  for (uint32_t i = threadIdx.x; i < cc.n; i += THREADS) {
+    cc.key[i] = SKEY_EMPTY;
+    cc.cnt[i] = 0;
+    cc.sum[i] = 0;
+    if (mm) {
+      cc.mn[i] = INT64_MAX;
+      cc.mx[i] = INT64_MIN;
+    }
+  }
+  if (threadIdx.x == 0) S.cache_used = 0;
+}
+
+// Writes the groups of the shared-memory table to the output and clears it.
+template <int ENT>
+__device__ uint32_t sub_emit(const HashParams& P, const Cache& cc, Smem& S, uint32_t level) {
+  const uint32_t per = cc.n / THREADS;  // consecutive slots per thread
+  const uint32_t i0 = threadIdx.x * per;
+  uint32_t oc = 0;
+  for (uint32_t i = 0; i < per; ++i) oc += cc.key[i0 + i] != SKEY_EMPTY;
+  uint32_t total;
+  const uint32_t off = block_exclusive_scan(oc, total, S);
+  if (threadIdx.x == 0) {
+    S.scan_base = total ? atomicAdd(&P.ctrl->out_count, (unsigned long long)total) : 0ull;
+    if (total) atomicAdd(&P.ctrl->resident_groups[level], (unsigned long long)total);
+  }
+  __syncthreads();
+  unsigned long long pos = S.scan_base + off;
+  for (uint32_t i = 0; i < per; ++i) {
+    const uint32_t j = i0 + i;
+    const long long key = cc.key[j];
+    if (key != SKEY_EMPTY) {
+      if (pos < P.o_cap) {
+        P.o_keys[pos] = key;
+        if (P.o_count) P.o_count[pos] = cc.cnt[j];
+        if (P.o_sum) P.o_sum[pos] = (long long)cc.sum[j];
+        if (Ent<ENT>::MM) {
+          if (P.o_min) P.o_min[pos] = cc.mn[j];
+          if (P.o_max) P.o_max[pos] = cc.mx[j];
+        }
+      } else {
+        set_status(P.ctrl, AGG_ERR_OUTPUT_CAPACITY);
+      }
+      ++pos;
+    }
+    cc.key[j] = SKEY_EMPTY;
+    cc.cnt[j] = 0;
+    cc.sum[j] = 0;
+    if (Ent<ENT>::MM) {
+      cc.mn[j] = INT64_MAX;
+      cc.mx[j] = INT64_MIN;
+    }
+  }
+  __syncthreads();
+  return total;
+}
+
+// Sub-partition of a record within its round (hash bits 16..31, independent of
+// the bucket bits 32..63, the tag bits 0..6 and the partition bits 8..15).
+__device__ __forceinline__ uint32_t sub_of(uint64_t h, uint32_t nsub) {
+  return (uint32_t)((((h >> 16) & 0xFFFFull) * nsub) >> 16);
+}
+
+// Loads record r of chunk-tile t of a round (one tile is one staging chunk).
+__device__ __forceinline__ bool load_chunk_record(const HashParams& P, uint32_t src, const uint32_t* list,
+                                                  const uint32_t* dcount, uint32_t c0, uint64_t t, int r,
+                                                  long long& k, long long& v) {
+  const uint32_t chunk = __ldcg(list + c0 + (uint32_t)t);
+  const uint32_t off = (uint32_t)r * THREADS + threadIdx.x;
+  if (off >= __ldcg(dcount + chunk)) return false;
+  const longlong2 rec = __ldcs(reinterpret_cast<const longlong2*>(P.stg[src] + ((size_t)chunk * CH + off) * REC_BYTES));
+  k = rec.x;
+  v = rec.y;
+  return true;
+}
+
+// One shared-memory round over the chunks [c0, c1) of the source area holding
+// `tot` records.  Pass A counts records per sub-partition; pass B scatters them
+// into the scratch memory grouped by sub-partition (exact offsets, cursors per
+// sub-partition); pass C lets each block aggregate whole sub-partitions in its
+// shared-memory table and emit them.  Keys that overflow a block's table go to
+// the level's global table G (or spill further).  Two grid barriers per round;
+// pass C needs none before the next round's pass A.
+template <int ENT>
+__device__ bool smem_round(const HashParams& P, const Level& G, Smem& S, const Cache& cc, uint32_t src, uint32_t c0,
+                           uint32_t c1, uint64_t tot, uint32_t par, longlong2* scratch) {
+  Ctrl* C = P.ctrl;
+  const uint32_t* dcount = P.dir_count[src];
+  const uint32_t* list = P.list[src];
+  const uint64_t ntiles = c1 - c0;
+  // sub-partitions sized by the keys-per-record of completed rounds of this parity
+  const double recd = (double)ld_relaxed_u64(&C->lvl_sub_records[par]);
+  const double grpd = (double)ld_relaxed_u64(&C->lvl_sub_groups[par]);
+  double est = recd > 0 ? 1.3 * grpd / recd + 0.02 : 1.0;
+  if (est > 1.0) est = 1.0;
+  const double subkeys = 0.55 * (double)cc.n;
+  uint64_t nsub = (uint64_t)((double)tot * est / subkeys) + 1;
+  const uint64_t nsub_cap = (2ull * cc.n < NSUB_MAX) ? 2ull * cc.n : NSUB_MAX;
+  if (nsub > nsub_cap) nsub = nsub_cap;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(cc.key);
+  uint32_t* base = reinterpret_cast<uint32_t*>(cc.key);
+  uint32_t* tcnt = reinterpret_cast<uint32_t*>(cc.cnt);
+  uint32_t* toff = reinterpret_cast<uint32_t*>(cc.sum);
+  const uint32_t lane = threadIdx.x & 31;
+
+  // ---- pass A: records per sub-partition
+  for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) hist[i] = 0;
+  __syncthreads();
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      long long k, v;
+      if (load_chunk_record(P, src, list, dcount, c0, t, r, k, v))
+        atomicAdd(&hist[sub_of(fmix64((uint64_t)k ^ G.seed), (uint32_t)nsub)], 1u);
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < nsub; i += THREADS)
+    if (hist[i]) atomicAdd(&C->sub_tot[par][i], hist[i]);
+  if (!grid_barrier(C, P.timeout_ns, S)) return false;
+
+  // ---- pass B: offsets, then scatter into scratch grouped by sub-partition
+  {
+    const uint32_t per = (uint32_t)((nsub + THREADS - 1) / THREADS);
+    const uint32_t s0 = threadIdx.x * per;
+    uint32_t mine = 0;
+    for (uint32_t i = 0; i < per; ++i)
+      if (s0 + i < nsub) mine += __ldcg(&C->sub_tot[par][s0 + i]);
+    uint32_t total;
+    uint32_t acc = block_exclusive_scan(mine, total, S);
+    for (uint32_t i = 0; i < per; ++i) {
+      if (s0 + i >= nsub) break;
+      base[s0 + i] = acc;
+      if (blockIdx.x == 0) C->sub_base[par][s0 + i] = acc;
+      acc += __ldcg(&C->sub_tot[par][s0 + i]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) C->sub_base[par][nsub] = total;
+    for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) tcnt[i] = 0;
+    __syncthreads();
+  }
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (threadIdx.x == 0 && t + gridDim.x < ntiles) {
+      const uint32_t nc = __ldcg(list + c0 + (uint32_t)(t + gridDim.x));
+      prefetch_l2(P.stg[src] + (size_t)nc * CH * REC_BYTES, __ldcg(dcount + nc) * (uint32_t)REC_BYTES);
+    }
+    long long k[RPT], v[RPT];
+    uint32_t sb[RPT], rk[RPT];
+    bool ok[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      ok[r] = load_chunk_record(P, src, list, dcount, c0, t, r, k[r], v[r]);
+      sb[r] = ok[r] ? sub_of(fmix64((uint64_t)k[r] ^ G.seed), (uint32_t)nsub) : 0u;
+      const uint32_t vm = __ballot_sync(FULL_MASK, ok[r]);
+      rk[r] = 0;
+      if (ok[r]) {
+        const uint32_t pm = __match_any_sync(vm, sb[r]);
+        const int ldr = __ffs(pm) - 1;
+        uint32_t b0 = 0;
+        if ((int)lane == ldr) b0 = atomicAdd(&tcnt[sb[r]], (uint32_t)__popc(pm));
+        b0 = __shfl_sync(pm, b0, ldr);
+        rk[r] = b0 + __popc(pm & lanemask_lt());
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) {
+      const uint32_t c = tcnt[i];
+      if (c) toff[i] = atomicAdd(&C->sub_cur[par][i], c);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (!ok[r]) continue;
+      longlong2 rec;
+      rec.x = k[r];
+      rec.y = v[r];
+      const uint64_t at = (uint64_t)base[sb[r]] + toff[sb[r]] + rk[r];
+      if (at < tot) scratch[at] = rec;
+      else set_status(C, AGG_ERR_INTERNAL);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) tcnt[i] = 0;
+    __syncthreads();
+  }
+  if (!grid_barrier(C, P.timeout_ns, S)) return false;
+
+  // ---- pass C: whole sub-partitions aggregated in shared memory
+  cache_reset_all(cc, S, Ent<ENT>::MM);
+  if (blockIdx.x == 0)  // counters of this parity are next used two rounds on
+    for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) {
+      C->sub_tot[par][i] = 0;
+      C->sub_cur[par][i] = 0;
+    }
+  __syncthreads();
+  unsigned long long my_recs = 0, my_groups = 0;
+  for (uint32_t sbi = blockIdx.x; sbi < nsub; sbi += gridDim.x) {
+    uint32_t lo = __ldcg(&C->sub_base[par][sbi]), hi = __ldcg(&C->sub_base[par][sbi + 1]);
+    if (hi > tot || lo > hi) {  // inconsistent offsets: report, never read past the scratch
+      if (threadIdx.x == 0) set_status(C, AGG_ERR_INTERNAL);
+      lo = hi = 0;
+    }
+    bool overflow = false;
+    for (uint32_t t0 = lo; t0 < hi; t0 += TILE) {
+      long long k[RPT], v[RPT];
+      bool need[RPT];
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const uint32_t i = t0 + (uint32_t)r * THREADS + threadIdx.x;
+        need[r] = false;
+        k[r] = 0;
+        v[r] = 0;
+        if (i < hi) {
+          const longlong2 rec = scratch[i];
+          k[r] = rec.x;
+          v[r] = rec.y;
+          need[r] = !sub_upsert<ENT>(cc, k[r], fmix64((uint64_t)k[r] ^ G.seed), v[r]);
+          overflow |= need[r];
+        }
+      }
+      global_and_spill<ENT>(P, G, S, cc, k, v, need, 0, false);
+    }
+    if (overflow) atomicOr(&C->overflow_used[G.level & 1], 1u);
+    __syncthreads();
+    my_groups += sub_emit<ENT>(P, cc, S, G.level);
+    my_recs += hi - lo;
+  }
+  if (threadIdx.x == 0 && my_recs) {
+    atomicAdd(&C->lvl_sub_records[par], my_recs);
+    atomicAdd(&C->lvl_sub_groups[par], my_groups);
+  }
+  cache_reset_all(cc, S, Ent<ENT>::MM);
+  __syncthreads();
+  return true;
+}
+
+// Restores the entries that served as scratch to the empty state.
+template <int ENT>
+__device__ void restore_scratch(const HashParams& P, uint32_t half) {
+  for (uint64_t s = half + blockIdx.x * (uint64_t)THREADS + threadIdx.x; s < P.slots;
+       s += (uint64_t)gridDim.x * THREADS)
+    Ent<ENT>::reset(Ent<ENT>::at(P.ent, (uint32_t)s));
+}
+
 // Last block to arrive publishes the group count and the run's statistics,
 // then zeroes the per-run control fields for the next run.
 __device__ void final_step(const HashParams& P, uint32_t levels) {
@@ -689,6 +1080,10 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
     S.cache_used = 0;
     S.spilled = 0;
     S.first_spill = 1;
+    S.tiles = 0;
+    S.use_cache = cc.n != 0 && P.cache != 0;
+    S.use_dedup = P.dedup;
+    S.st_rows = S.st_hits = S.st_dups = 0;
   }
   __syncthreads();
 
@@ -703,6 +1098,16 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
     const uint64_t ntiles = (P.n + TILE - 1) / TILE;
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const uint64_t row0 = t * TILE;
+      if (threadIdx.x == 0 && P.vec_ok && t + gridDim.x < ntiles) {  // stage this block's next tile in L2
+        const uint64_t nr0 = (t + gridDim.x) * TILE;
+        const uint64_t nrows = P.n - nr0 < (uint64_t)TILE ? P.n - nr0 : (uint64_t)TILE;
+        prefetch_l2(P.keys + nr0, (uint32_t)(nrows * 8));
+        if (P.has_vals)
+          prefetch_l2(static_cast<const char*>(P.vals) + nr0 * (VT == AGG_I64 ? 8 : 4),
+                      (uint32_t)(nrows * (VT == AGG_I64 ? 8 : 4)));
+      }
+      adapt_begin_tile(S, cc.n != 0 && P.cache != 0, P.dedup != 0);
+      __syncthreads();
       long long k[RPT], v[RPT];
       bool valid[RPT];
 #pragma unroll
@@ -741,6 +1146,7 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
         }
       }
       process_rows<ENT>(P, L, S, cc, k, v, valid, row0);
+      adapt_end_tile(S, cc.n != 0 && P.cache != 0, P.dedup != 0);
     }
     cache_flush<ENT>(P, cc, S);
     finalize_chunks(P, S, 0, 0);
@@ -770,9 +1176,18 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
     uint32_t* dpart = P.dir_part[src];
     uint32_t* dcount = P.dir_count[src];
     uint32_t* list = P.list[src];
-    // P1: per-partition chunk and record counts of the source area
-    if (threadIdx.x == 0 && blockIdx.x == 0) C->pool_next[dst] = 0;
-    const unsigned long long nch = ld_relaxed_u64(&C->pool_next[src]);
+    // P1: per-partition chunk and record counts of the source area.  Block 0
+    // also clears the level's round counters here, before the level's first
+    // barrier, so every block later reads the same values.
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+      C->pool_next[dst] = 0;
+      C->overflow_used[level & 1] = 0;
+      C->lvl_sub_records[0] = C->lvl_sub_records[1] = 0;
+      C->lvl_sub_groups[0] = C->lvl_sub_groups[1] = 0;
+    }
+    // chunks handed out (a failed allocation still advanced the cursor)
+    unsigned long long nch = ld_relaxed_u64(&C->pool_next[src]);
+    if (nch > P.max_chunks[src]) nch = P.max_chunks[src];
     for (uint32_t p = threadIdx.x; p < MAX_FAN; p += THREADS) {
       S.cnt[p] = 0;
       S.hrec[p] = 0;
@@ -818,62 +1233,69 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
       }
     }
     tm.lap(C, PH_LISTS);
-    // Rounds: consecutive partitions packed while their records fit the table.
-    const uint64_t cap_full = (uint64_t)(P.lf * (double)P.slots);
+    // Rounds.  At levels >= 1 the global table keeps the lower half of the
+    // slots (keys that overflow shared memory, partitions too big for a
+    // shared-memory round) and the upper half of the entry memory serves as
+    // sub-partition scratch.  Whole partitions are packed into each round.
+    const uint32_t half = (P.slots / 2) / BUCKET * BUCKET;
+    longlong2* scratch = reinterpret_cast<longlong2*>(P.ent + (size_t)half * Ent<ENT>::ES);
+    const uint64_t scratch_recs = ((uint64_t)(P.slots - half) * Ent<ENT>::ES) / REC_BYTES;
+    const uint64_t round_cap = scratch_recs < ROUND_CAP_MAX ? scratch_recs : ROUND_CAP_MAX;
+    const bool smem_ok = cc.n >= (uint32_t)THREADS && round_cap >= (uint64_t)TILE;
+    Level G;
+    G.level = level;
+    G.seed = level_seed(P.seed, level);
+    G.s_act = half;
+    G.dst = dst;
+    G.fan_mask = fan - 1;
+    uint32_t rnd = 0;
     uint32_t p = 0;
     while (true) {
       while (p < fan && __ldcg(&C->part_records[set][p]) == 0) ++p;
       if (p >= fan) break;
       uint64_t tot = __ldcg(&C->part_records[set][p]);
       uint32_t q = p + 1;
-      while (q < fan) {
-        const uint64_t r = __ldcg(&C->part_records[set][q]);
-        if (tot + r > cap_full) break;
-        tot += r;
-        ++q;
+      if (smem_ok && tot <= round_cap) {
+        while (q < fan) {
+          const uint64_t r = __ldcg(&C->part_records[set][q]);
+          if (tot + r > round_cap) break;
+          tot += r;
+          ++q;
+        }
+        if (!smem_round<ENT>(P, G, S, cc, src, S.begin[p], S.begin[q], tot, rnd & 1, scratch)) return;
+        if (threadIdx.x == 0 && blockIdx.x == 0) C->rounds += 1;
+        ++rnd;
+        tm.lap(C, PH_ROUND_AGG);
+        p = q;
+        continue;
       }
-      Level L;
-      L.level = level;
-      L.seed = level_seed(P.seed, level);
-      uint64_t want = (uint64_t)((double)tot / P.lf) + BUCKET;
-      want = (want + BUCKET - 1) / BUCKET * BUCKET;
-      if (want < MIN_SLOTS) want = MIN_SLOTS;
-      if (want > P.slots) want = P.slots;
-      L.s_act = (uint32_t)want;
-      L.dst = dst;
-      L.fan_mask = fan - 1;
+      // a partition too big for a shared-memory round: global-table round
       const uint32_t c0 = S.begin[p], c1 = S.begin[q];
-      const uint64_t nrec_slots = (uint64_t)(c1 - c0) * CH;
-      const uint64_t ntiles = (nrec_slots + TILE - 1) / TILE;
+      const uint64_t ntiles = c1 - c0;
+      if (!grid_barrier(C, P.timeout_ns, S)) return;  // shared-memory rounds before it are complete
       for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (threadIdx.x == 0 && t + gridDim.x < ntiles) {  // one tile is one chunk (CH == TILE)
+          const uint32_t nc = __ldcg(list + c0 + (uint32_t)(t + gridDim.x));
+          prefetch_l2(P.stg[src] + (size_t)nc * CH * REC_BYTES, __ldcg(dcount + nc) * (uint32_t)REC_BYTES);
+        }
+        adapt_begin_tile(S, cc.n != 0 && P.cache != 0, P.dedup != 0);
+        __syncthreads();
         long long k[RPT], v[RPT];
         bool valid[RPT];
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
-          const uint64_t g = t * TILE + (uint64_t)r * THREADS + threadIdx.x;
-          valid[r] = false;
           k[r] = 0;
           v[r] = 0;
-          if (g < nrec_slots) {
-            const uint32_t ci = c0 + (uint32_t)(g / CH);
-            const uint32_t off = (uint32_t)(g % CH);
-            const uint32_t chunk = __ldcg(list + ci);
-            if (off < __ldcg(dcount + chunk)) {
-              const longlong2 rec = __ldcs(reinterpret_cast<const longlong2*>(
-                  P.stg[src] + ((size_t)chunk * CH + off) * REC_BYTES));
-              k[r] = rec.x;
-              v[r] = rec.y;
-              valid[r] = true;
-            }
-          }
+          valid[r] = load_chunk_record(P, src, list, dcount, c0, t, r, k[r], v[r]);
         }
-        process_rows<ENT>(P, L, S, cc, k, v, valid, 0);
+        process_rows<ENT>(P, G, S, cc, k, v, valid, 0);
+        adapt_end_tile(S, cc.n != 0 && P.cache != 0, P.dedup != 0);
       }
       cache_flush<ENT>(P, cc, S);
       tm.lap(C, PH_ROUND_AGG);
       if (!grid_barrier(C, P.timeout_ns, S)) return;
       tm.lap(C, PH_ROUND_WAIT);
-      emit_table<ENT>(P, L.s_act, level, S);
+      emit_table<ENT>(P, half, level, S);
       if (threadIdx.x == 0 && blockIdx.x == 0) C->rounds += 1;
       tm.lap(C, PH_ROUND_EMIT);
       if (!grid_barrier(C, P.timeout_ns, S)) return;
@@ -883,7 +1305,10 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
     finalize_chunks(P, S, dst, level);
     if (!grid_barrier(C, P.timeout_ns, S)) return;
     tm.lap(C, PH_ROUND_WAIT);
+    if (ld_acquire_u32(&C->overflow_used[level & 1])) emit_table<ENT>(P, half, level, S);
+    tm.lap(C, PH_ROUND_EMIT);
     if (ld_relaxed_u64(&C->pool_next[dst]) == 0) {
+      restore_scratch<ENT>(P, half);
       total.lap(C, PH_TOTAL);
       final_step(P, level + 1);
       return;
