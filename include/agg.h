@@ -189,6 +189,31 @@ agg_status agg_destroy(agg_handle* h);
 /* Static description of a status code. */
 const char* agg_strerror(agg_status s);
 
+/* Size of the fixed working memory of agg_run_noalloc. */
+#define AGG_NOALLOC_SLOTS (1u << 18)
+#define AGG_NOALLOC_MAX_ROWS ((uint64_t)AGG_NOALLOC_SLOTS / 4)
+
+/* The in-budget hash group-by for callers that cannot allocate device memory.
+ * The paper has no counterpart: it is an addition for callers that may not
+ * call cudaMalloc or cudaFree at all, such as code running inside a framework
+ * that owns every device allocation, or code on a latency-critical path that
+ * cannot afford an allocation or the device-wide synchronisation of a free.
+ * Nothing is allocated: the working memory (about 17 MB: control block, tag
+ * bytes and AGG_NOALLOC_SLOTS table entries) is a file-scope __device__ array
+ * of libagg.so that every GPU loading the library holds until the process
+ * exits.  n may be at most AGG_NOALLOC_MAX_ROWS (else AGG_ERR_INVALID_ARG, and
+ * nothing runs), which keeps every group resident with no staging area.
+ * spec: as for agg_create, with path AGG_PATH_HASH.  d_keys, d_vals, out: as
+ * for agg_run (device pointers, caller-owned).  The call enqueues the work on
+ * `stream`, waits for it, and returns the run's status, with the group count in
+ * *n_groups (may be NULL).  The first call on a device sets that device up (it
+ * looks up the array's device address and the kernel's launch shape), so make
+ * it before any stream capture.  Every call shares the one array and clears it
+ * first: calls whose work overlaps on the GPU (other streams, other threads)
+ * race on it and must be serialised by the caller. */
+agg_status agg_run_noalloc(const agg_spec* spec, const int64_t* d_keys, const void* d_vals, uint64_t n,
+                           const agg_output* out, uint64_t* n_groups, void* stream);
+
 /* Host-only planning: the table size, capacity and fan-out agg_create/agg_run
  * would choose for this budget, spec and n (Eq. 1 adapted to bytes, Section
  * 4.3).  No GPU is touched.  Errors: AGG_ERR_INVALID_ARG,

@@ -84,7 +84,12 @@ SIGNATURES = {
     "agg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "agg_plan": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(agg_spec), ctypes.POINTER(agg_tuning), _U64,
                                 ctypes.POINTER(agg_plan_info)]),
+    "agg_run_noalloc": (ctypes.c_int, [ctypes.POINTER(agg_spec), _P, _P, _U64, ctypes.POINTER(agg_output),
+                                       ctypes.POINTER(_U64), _P]),
 }
+
+AGG_NOALLOC_SLOTS = 1 << 18
+AGG_NOALLOC_MAX_ROWS = AGG_NOALLOC_SLOTS // 4
 
 _LIB = None
 
