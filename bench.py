@@ -44,7 +44,9 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="spill", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="spill", choices=sorted(WORKLOADS) + ["batched"])
+    ap.add_argument("--instances", type=int, default=4096, help="instances of the batched workload")
+    ap.add_argument("--tune", action="store_true", help="batched: run the autotuner and store its winner")
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--domain", type=int, default=0)
     ap.add_argument("--budget", type=int, default=0)
@@ -409,10 +411,122 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ batched workload
+
+def run_batched(args):
+    """4,096 independent instances in one persistent launch (CUDA graph replay)
+    against the plain loop of one agg_run per instance, at identical output."""
+    import torch
+    from paper_1311_0059_gb300 import AGG_I64, autotune
+    from paper_1311_0059_gb300.groupby import Batch, GroupBy
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ws = dg.batch_workloads(args.instances, seed=rank)
+    inst = []
+    for w in ws:
+        k = torch.empty(w.n, dtype=torch.int64, device=dev)
+        v = torch.empty(w.n, dtype=torch.int64, device=dev)
+        cdf = torch.from_numpy(w.cdf()).to(dev) if w.dist == "zipf" else None
+        w.device(k.data_ptr(), v.data_ptr(), cdf_ptr=cdf.data_ptr() if cdf is not None else 0,
+                 stream_handle=stream.cuda_stream)
+        inst.append((k, v, w.budget, 0))
+    torch.cuda.synchronize()
+    caps = [min(w.n, w.domain) for w in ws]  # a group per distinct key at most
+    rows = sum(w.n for w in ws)
+    wclass = f"batched-{args.instances}"
+
+    def make(t):
+        return Batch(inst, ops=15, value_type=AGG_I64, tuning=t, capacities=caps)
+
+    tuning = None if args.tune else autotune.lookup(wclass)
+    tune_info = None
+    if tuning is None:
+        best, trials = autotune.tune_batch(make, reps=2, log=lambda m: print(m, file=sys.stderr))
+        autotune.store(wclass, best, trials)
+        tuning = autotune.lookup(wclass)
+        tune_info = {"trials": len(trials), "best": best}
+    b = make(tuning)
+    for _ in range(max(args.warmup, 1)):
+        assert b.run_async(stream) == 0
+    counts_b = b.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            assert b.run_async(stream) == 0
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms_batch = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
+    b.sync()
+
+    # plain loop: one agg_run per instance on handles whose budget is the
+    # instance's budget rounded up to a power of two MiB (never less memory)
+    handles = {}
+
+    def handle_for(budget):
+        mb = 4
+        while (mb << 20) < budget:
+            mb *= 2
+        if mb not in handles:
+            h = GroupBy(mb << 20, ops=15, value_type=AGG_I64)
+            h.reserve(max(w.n for w in ws))
+            handles[mb] = h
+        return handles[mb]
+
+    outs = b.outs
+
+    def plain_pass():
+        for (k, v, bud, _), o, w in zip(inst, outs, ws):
+            assert handle_for(bud).run_async(k, v, o, w.n, stream) == 0
+
+    plain_pass()
+    torch.cuda.synchronize()
+    counts_p = [int(o.n_groups.item()) for o in outs]
+    reps_plain = max(1, min(3, args.steps))
+    ev0.record(stream)
+    for _ in range(reps_plain):
+        plain_pass()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    for h in handles.values():
+        h.sync()
+    ms_plain = max_over_ranks(ev0.elapsed_time(ev1) / reps_plain, world, dev)
+    rows_all = sum_over_ranks(float(rows), world, dev)
+    line = {"metric": "batched group-by rows/s (4,096 instances, one persistent launch)",
+            "value": rows_all / (ms_batch / 1e3), "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded, generated on the device)",
+            "config": {"workload": f"batched: {args.instances} instances, rows log-uniform [1e3, 4e6], "
+                                   "distinct 1-50% of rows, uniform or Zipf(s in [0.5,1.2]), budgets "
+                                   "log-uniform [4, 64] MiB, COUNT+SUM+MIN+MAX", "rows": rows,
+                       "team_blocks": tuning.team_blocks, "smem_entries": tuning.smem_entries,
+                       "max_load_factor": tuning.max_load_factor},
+            "plain_loop": {"rows_per_s": rows_all / (ms_plain / 1e3), "ms_per_pass": ms_plain,
+                           "launches_per_pass": len(ws)},
+            "speedup_vs_plain": ms_plain / ms_batch, "identical_group_counts": counts_b == counts_p,
+            "gpu_launches": args.steps, "clocks": clocks.summary()}
+    if tune_info:
+        line["autotune"] = tune_info
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+    for h in handles.values():
+        h.close()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -45,6 +45,7 @@ STREAM_KEY = 0
 STREAM_VAL = 1
 STREAM_SALT = 2
 STREAM_INSTANCE = 3
+STREAM_PARAMS = 4
 
 _U64 = np.uint64
 
@@ -239,3 +240,29 @@ def _device_lib():
                                      ctypes.c_void_p, ctypes.c_void_p]
         _LIB = lib
     return _LIB
+
+
+def unit_doubles(seed: int, sid: int, count: int) -> np.ndarray:
+    """count doubles in [0, 1) from stream ``sid``: (u >> 11) * 2**-53."""
+    return (stream(seed, sid, 0, count) >> _U64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def batch_workloads(count: int = 4096, seed: int = 0, rows=(1_000, 4_000_000), card=(0.01, 0.50),
+                    budget=(4 << 20, 64 << 20), zipf_s=(0.5, 1.2)) -> list:
+    """The batched workload: `count` independent group-by instances.  Per
+    instance (five draws of stream 4 under `seed`): rows log-uniform in `rows`,
+    distinct keys a uniform fraction `card` of the rows, uniform or Zipf keys
+    (probability 1/2 each) with Zipf exponent uniform in `zipf_s`, int64 values
+    in [0, 2**20), COUNT+SUM+MIN+MAX, budget log-uniform in `budget`."""
+    u = unit_doubles(seed, STREAM_PARAMS, 5 * count).reshape(count, 5)
+    out = []
+    for i in range(count):
+        n = int(np.exp(np.log(rows[0]) + u[i, 0] * (np.log(rows[1]) - np.log(rows[0]))))
+        frac = card[0] + u[i, 1] * (card[1] - card[0])
+        dom = max(1, int(round(frac * n)))
+        zipf = u[i, 2] < 0.5
+        s = zipf_s[0] + u[i, 3] * (zipf_s[1] - zipf_s[0])
+        b = int(np.exp(np.log(budget[0]) + u[i, 4] * (np.log(budget[1]) - np.log(budget[0]))))
+        out.append(Workload(f"batch instance {i}", n=n, domain=dom, dist="zipf" if zipf else "uniform",
+                            zipf_s=float(s), vtype="i64_2p20", seed=instance_seed(seed, i), budget=b, ops=15))
+    return out

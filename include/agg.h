@@ -189,6 +189,53 @@ agg_status agg_destroy(agg_handle* h);
 /* Static description of a status code. */
 const char* agg_strerror(agg_status s);
 
+/* ---- Batched form: many independent group-bys in one persistent launch ---- */
+
+/* One instance of a batch: its input, its working-memory budget and its output
+ * (device pointers, caller-owned; out.d_n_groups is ignored: the counts are
+ * returned by agg_batch_sync). */
+typedef struct agg_batch_item {
+  const int64_t* d_keys;
+  const void* d_vals;
+  uint64_t n;
+  size_t budget;            /* this instance's budget, >= AGG_MIN_BUDGET */
+  uint64_t expected_groups; /* optional estimate of its result size; 0 = unknown */
+  agg_output out;
+} agg_batch_item;
+
+/* Knobs of the batch; zero fields keep the defaults (or the tuning table). */
+typedef struct agg_batch_tuning {
+  uint32_t team_blocks;    /* thread blocks that run one instance together (power of two) */
+  uint32_t smem_entries;   /* shared-memory table entries per block (power of two, >= 512) */
+  double max_load_factor;
+  uint32_t fan_out;
+  uint32_t use_graph;      /* 0 = default (capture the launch in a CUDA graph), 2 = launch directly */
+} agg_batch_tuning;
+
+typedef struct agg_batch agg_batch;
+
+/* Plans a batch of `count` instances sharing spec.ops and spec.value_type
+ * (spec.path must be AGG_PATH_HASH): instances are assigned to teams of thread
+ * blocks longest-first; every team owns working memory large enough for the
+ * largest budget among its instances (each instance uses at most its own
+ * budget of it, one instance at a time) and staging for those that may spill.
+ * Allocates everything the runs need.  Errors: AGG_ERR_INVALID_ARG,
+ * AGG_ERR_BUDGET_TOO_SMALL (an item's budget), AGG_ERR_OOM, AGG_ERR_CUDA. */
+agg_status agg_batch_create(const agg_spec* spec, const agg_batch_item* items, uint32_t count,
+                            const agg_batch_tuning* t, agg_batch** out);
+
+/* Runs every instance of the batch with one cooperative kernel launch (replayed
+ * from a CUDA graph captured on the first run), asynchronously on `stream`. */
+agg_status agg_batch_run(agg_batch* b, void* stream);
+
+/* Waits for the last run; stores each instance's group count in n_groups[i]
+ * (host array of `count` entries, may be NULL) and returns the first device-side
+ * error of any instance. */
+agg_status agg_batch_sync(agg_batch* b, uint64_t* n_groups);
+
+/* Releases the batch (waits for its work first).  NULL is allowed. */
+agg_status agg_batch_destroy(agg_batch* b);
+
 /* Size of the fixed working memory of agg_run_noalloc. */
 #define AGG_NOALLOC_SLOTS (1u << 18)
 #define AGG_NOALLOC_MAX_ROWS ((uint64_t)AGG_NOALLOC_SLOTS / 4)

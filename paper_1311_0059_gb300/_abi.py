@@ -71,6 +71,16 @@ class agg_plan_info(ctypes.Structure):
                 ("active_slots", _U64), ("working_bytes", _U64), ("staging_bytes", _U64)]
 
 
+class agg_batch_item(ctypes.Structure):
+    _fields_ = [("d_keys", _P), ("d_vals", _P), ("n", _U64), ("budget", ctypes.c_size_t),
+                ("expected_groups", _U64), ("out", agg_output)]
+
+
+class agg_batch_tuning(ctypes.Structure):
+    _fields_ = [("team_blocks", ctypes.c_uint32), ("smem_entries", ctypes.c_uint32),
+                ("max_load_factor", ctypes.c_double), ("fan_out", ctypes.c_uint32), ("use_graph", ctypes.c_uint32)]
+
+
 # name -> (restype, argtypes); the names are exactly those declared in include/agg.h
 SIGNATURES = {
     "agg_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(agg_spec), ctypes.POINTER(_P)]),
@@ -86,6 +96,11 @@ SIGNATURES = {
                                 ctypes.POINTER(agg_plan_info)]),
     "agg_run_noalloc": (ctypes.c_int, [ctypes.POINTER(agg_spec), _P, _P, _U64, ctypes.POINTER(agg_output),
                                        ctypes.POINTER(_U64), _P]),
+    "agg_batch_create": (ctypes.c_int, [ctypes.POINTER(agg_spec), ctypes.POINTER(agg_batch_item), ctypes.c_uint32,
+                                        ctypes.POINTER(agg_batch_tuning), ctypes.POINTER(_P)]),
+    "agg_batch_run": (ctypes.c_int, [_P, _P]),
+    "agg_batch_sync": (ctypes.c_int, [_P, ctypes.POINTER(_U64)]),
+    "agg_batch_destroy": (ctypes.c_int, [_P]),
 }
 
 AGG_NOALLOC_SLOTS = 1 << 18

@@ -3,7 +3,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <queue>
+#include <vector>
 
 #include "agg_internal.cuh"
 #include "sort_path.cuh"
@@ -621,6 +624,302 @@ agg_status agg_destroy(agg_handle* h) {
   if (h->out_buf) cudaFree(h->out_buf);
   if (h->ng_host) cudaFreeHost(h->ng_host);
   delete h;
+  return AGG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batched form
+
+struct agg_batch {
+  int device = 0;
+  agg_spec spec{};
+  int ent_kind = 0;
+  uint32_t es = 32;
+  uint32_t count = 0;
+  uint32_t team_blocks = 4, nteams = 0;
+  KernelInfo ki{};
+  void* work = nullptr;     // all teams' working memory
+  void* staging = nullptr;  // all teams' staging areas
+  HashParams* d_items = nullptr;
+  uint32_t* d_team_off = nullptr;
+  uint32_t* d_team_items = nullptr;
+  unsigned long long* d_ngroups = nullptr;
+  std::vector<Ctrl*> ctrl;
+  std::vector<uint8_t*> team_ent;
+  std::vector<uint32_t*> team_tags;
+  std::vector<uint32_t> team_slots;
+  cudaGraphExec_t exec = nullptr;
+  bool use_graph = true;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+agg_status batch_init_teams(agg_batch* b) {
+  for (uint32_t t = 0; t < b->nteams; ++t) {
+    if (cudaMemset(b->ctrl[t], 0, sizeof(Ctrl)) != cudaSuccess ||
+        hash_init_table(b->team_ent[t], b->team_tags[t], b->team_slots[t], b->ent_kind, nullptr) != cudaSuccess)
+      return AGG_ERR_CUDA;
+  }
+  return cudaDeviceSynchronize() == cudaSuccess ? AGG_OK : AGG_ERR_CUDA;
+}
+
+agg_status batch_launch(agg_batch* b, cudaStream_t s) {
+  return hash_batch_launch(b->ent_kind, b->spec.value_type, b->d_items, b->d_team_off, b->d_team_items,
+                           b->team_blocks, b->nteams, b->ki.smem, s) == cudaSuccess
+             ? AGG_OK
+             : AGG_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+agg_status agg_batch_create(const agg_spec* spec, const agg_batch_item* items, uint32_t count,
+                            const agg_batch_tuning* t, agg_batch** out) {
+  if (!out || !valid_spec(spec) || spec->path != AGG_PATH_HASH || (count > 0 && !items)) return AGG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (t && ((t->team_blocks & (t->team_blocks - 1)) || (t->smem_entries && (t->smem_entries < 512 ||
+      t->smem_entries > 4096 || (t->smem_entries & (t->smem_entries - 1)))) || t->max_load_factor < 0 ||
+      t->max_load_factor > 0.95 || (t->fan_out && (t->fan_out < 16 || t->fan_out > 256 ||
+      (t->fan_out & (t->fan_out - 1)))) || t->use_graph > 2))
+    return AGG_ERR_INVALID_ARG;
+  agg_batch* b = new (std::nothrow) agg_batch();
+  if (!b) return AGG_ERR_OOM;
+  auto fail = [&](agg_status st) {
+    agg_batch_destroy(b);
+    return st;
+  };
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return AGG_ERR_CUDA;
+  }
+  b->spec = *spec;
+  b->count = count;
+  b->ent_kind = pick_ent(spec);
+  b->es = entry_bytes(b->ent_kind);
+  b->use_graph = !(t && t->use_graph == 2);
+  agg_tuning tune = effective(nullptr);
+  if (t && t->smem_entries) tune.smem_entries = t->smem_entries;
+  if (t && t->max_load_factor > 0) tune.max_load_factor = t->max_load_factor;
+  if (t && t->fan_out) tune.fan_out = t->fan_out;
+  if (hash_batch_kernel_info(b->ent_kind, spec->value_type, tune.smem_entries, b->device, &b->ki) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AGG_ERR_CUDA);
+  }
+  b->team_blocks = (t && t->team_blocks) ? t->team_blocks : 4;
+  while (b->team_blocks > 1 && (uint32_t)b->ki.blocks < b->team_blocks) b->team_blocks >>= 1;
+  b->nteams = (uint32_t)b->ki.blocks / b->team_blocks;
+
+  // per-instance plan
+  struct Plan {
+    uint64_t slots, fan, s_act0;
+    bool may_spill;
+  };
+  std::vector<Plan> plan(count);
+  for (uint32_t i = 0; i < count; ++i) {
+    if (items[i].n > 0 && !is_device_ptr(items[i].d_keys)) return fail(AGG_ERR_INVALID_ARG);
+    if (!items[i].out.keys || !is_device_ptr(items[i].out.keys)) return fail(AGG_ERR_INVALID_ARG);
+    Layout L;
+    if (!layout_for(items[i].budget, b->es, &L)) return fail(AGG_ERR_BUDGET_TOO_SMALL);
+    agg_spec si = *spec;
+    si.expected_groups = items[i].expected_groups;
+    const uint64_t est = si.expected_groups ? si.expected_groups : (items[i].n ? items[i].n : 1);
+    uint64_t need = (uint64_t)((double)(items[i].n ? items[i].n : 1) / tune.max_load_factor) + BUCKET;
+    need = std::max<uint64_t>((need + BUCKET - 1) / BUCKET * BUCKET, 2 * MIN_SLOTS);
+    plan[i].slots = std::min<uint64_t>(L.slots, need);  // never more than the input can use
+    plan[i].s_act0 = active_slots(est, tune.max_load_factor, plan[i].slots);
+    plan[i].fan = plan_fan(&si, tune, items[i].n, items[i].budget, b->es);
+    plan[i].may_spill = items[i].n > (uint64_t)(0.5 * (double)plan[i].slots);
+  }
+  // teams: longest first onto the least loaded team (each instance also costs a fixed overhead)
+  std::vector<uint32_t> order(count);
+  for (uint32_t i = 0; i < count; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) { return items[a].n > items[c].n; });
+  using Load = std::pair<double, uint32_t>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (uint32_t tm = 0; tm < b->nteams; ++tm) heap.push({0.0, tm});
+  std::vector<std::vector<uint32_t>> lists(b->nteams);
+  for (uint32_t i : order) {
+    Load l = heap.top();
+    heap.pop();
+    lists[l.second].push_back(i);
+    l.first += (double)items[i].n + 20000.0;
+    heap.push(l);
+  }
+  // memory: per team, room for its largest table and its largest spilling input
+  std::vector<uint64_t> slots_t(b->nteams, 2 * MIN_SLOTS), rows_t(b->nteams, 0), fan_t(b->nteams, 16);
+  for (uint32_t tm = 0; tm < b->nteams; ++tm)
+    for (uint32_t i : lists[tm]) {
+      slots_t[tm] = std::max<uint64_t>(slots_t[tm], plan[i].slots);
+      if (plan[i].may_spill) rows_t[tm] = std::max<uint64_t>(rows_t[tm], items[i].n);
+      fan_t[tm] = std::max<uint64_t>(fan_t[tm], plan[i].fan);
+    }
+  const uint64_t ctrl_bytes = align_up(sizeof(Ctrl), 256);
+  std::vector<uint64_t> woff(b->nteams + 1, 0), soff(b->nteams + 1, 0), chunks_t(b->nteams, 0);
+  for (uint32_t tm = 0; tm < b->nteams; ++tm) {
+    const uint64_t tags = align_up(slots_t[tm] + BUCKET, 256);
+    woff[tm + 1] = woff[tm] + align_up(ctrl_bytes + tags + (slots_t[tm] + 1) * b->es, 256);
+    if (rows_t[tm]) chunks_t[tm] = (rows_t[tm] + CH - 1) / CH + (uint64_t)b->team_blocks * fan_t[tm] + 8;
+    const uint64_t per_area = align_up(chunks_t[tm] * CH * REC_BYTES, 256) + 3 * align_up(chunks_t[tm] * 4, 256);
+    soff[tm + 1] = soff[tm] + 2 * per_area;
+  }
+  if (cudaMalloc(&b->work, std::max<uint64_t>(woff[b->nteams], 256)) != cudaSuccess ||
+      (soff[b->nteams] && cudaMalloc(&b->staging, soff[b->nteams]) != cudaSuccess) ||
+      cudaMalloc(&b->d_ngroups, std::max<uint64_t>(count, 1) * 8) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AGG_ERR_OOM);
+  }
+  b->ctrl.resize(b->nteams);
+  b->team_ent.resize(b->nteams);
+  b->team_tags.resize(b->nteams);
+  b->team_slots.resize(b->nteams);
+  std::vector<HashParams> hp(count);
+  for (uint32_t tm = 0; tm < b->nteams; ++tm) {
+    uint8_t* base = static_cast<uint8_t*>(b->work) + woff[tm];
+    const uint64_t tags = align_up(slots_t[tm] + BUCKET, 256);
+    b->ctrl[tm] = reinterpret_cast<Ctrl*>(base);
+    b->team_tags[tm] = reinterpret_cast<uint32_t*>(base + ctrl_bytes);
+    b->team_ent[tm] = base + ctrl_bytes + tags;
+    b->team_slots[tm] = (uint32_t)slots_t[tm];
+    uint8_t* stg = b->staging ? static_cast<uint8_t*>(b->staging) + soff[tm] : nullptr;
+    const uint64_t data = align_up(chunks_t[tm] * CH * REC_BYTES, 256), meta = align_up(chunks_t[tm] * 4, 256);
+    for (uint32_t i : lists[tm]) {
+      HashParams& p = hp[i];
+      const agg_batch_item& it = items[i];
+      p.keys = it.d_keys;
+      p.vals = it.d_vals;
+      p.n = it.n;
+      p.has_vals = it.d_vals != nullptr;
+      p.vec_ok = ((reinterpret_cast<uintptr_t>(it.d_keys) & 15) == 0) &&
+                 (!it.d_vals || (reinterpret_cast<uintptr_t>(it.d_vals) & (spec->value_type == AGG_I64 ? 15 : 7)) == 0);
+      p.o_keys = it.out.keys;
+      p.o_count = (spec->ops & AGG_COUNT) ? it.out.count : nullptr;
+      p.o_sum = (spec->ops & AGG_SUM) ? it.out.sum : nullptr;
+      p.o_min = (spec->ops & AGG_MIN) ? it.out.min : nullptr;
+      p.o_max = (spec->ops & AGG_MAX) ? it.out.max : nullptr;
+      p.o_cap = it.out.capacity;
+      p.o_ngroups = reinterpret_cast<uint64_t*>(b->d_ngroups + i);
+      p.ctrl = b->ctrl[tm];
+      p.ent = b->team_ent[tm];
+      p.tags = b->team_tags[tm];
+      p.slots = (uint32_t)plan[i].slots;
+      for (int a = 0; a < 2; ++a) {
+        uint8_t* area = stg ? stg + a * (data + 3 * meta) : nullptr;
+        p.stg[a] = area;
+        p.dir_part[a] = area ? reinterpret_cast<uint32_t*>(area + data) : nullptr;
+        p.dir_count[a] = area ? reinterpret_cast<uint32_t*>(area + data + meta) : nullptr;
+        p.list[a] = area ? reinterpret_cast<uint32_t*>(area + data + 2 * meta) : nullptr;
+        p.max_chunks[a] = area ? chunks_t[tm] : 0;
+      }
+      p.seed = spec->seed + i;
+      p.ops = spec->ops;
+      p.fan_log2 = log2u((uint32_t)plan[i].fan);
+      p.lf = tune.max_load_factor;
+      p.s_act0 = (uint32_t)plan[i].s_act0;
+      p.ns = tune.smem_entries;
+      p.cache = 1;
+      p.dedup = 1;
+      p.timeout_ns = TIMEOUT_NS;
+    }
+  }
+  std::vector<uint32_t> toff(b->nteams + 1, 0), titems;
+  titems.reserve(count);
+  for (uint32_t tm = 0; tm < b->nteams; ++tm) {
+    toff[tm + 1] = toff[tm] + (uint32_t)lists[tm].size();
+    titems.insert(titems.end(), lists[tm].begin(), lists[tm].end());
+  }
+  if (cudaMalloc(&b->d_items, std::max<uint64_t>(count, 1) * sizeof(HashParams)) != cudaSuccess ||
+      cudaMalloc(&b->d_team_off, (b->nteams + 1) * 4) != cudaSuccess ||
+      cudaMalloc(&b->d_team_items, std::max<uint64_t>(count, 1) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AGG_ERR_OOM);
+  }
+  if ((count && cudaMemcpy(b->d_items, hp.data(), count * sizeof(HashParams), cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(b->d_team_off, toff.data(), (b->nteams + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (count && cudaMemcpy(b->d_team_items, titems.data(), count * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemset(b->d_ngroups, 0, std::max<uint64_t>(count, 1) * 8) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AGG_ERR_CUDA);
+  }
+  agg_status st = batch_init_teams(b);
+  if (st != AGG_OK) return fail(st);
+  *out = b;
+  return AGG_OK;
+}
+
+agg_status agg_batch_run(agg_batch* b, void* stream) {
+  if (!b) return AGG_ERR_INVALID_ARG;
+  DeviceGuard g(b->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  b->last_stream = s;
+  if (b->use_graph && !b->exec) {
+    // capture the one launch of the batch kernel as a graph, once
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const agg_status ls = batch_launch(b, cs);
+      ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && ls == AGG_OK && graph &&
+           cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    if (!ok) {
+      cudaGetLastError();
+      b->exec = nullptr;
+      b->use_graph = false;  // launch directly from now on
+    }
+  }
+  if (b->exec) return cudaGraphLaunch(b->exec, s) == cudaSuccess ? AGG_OK : AGG_ERR_CUDA;
+  return batch_launch(b, s);
+}
+
+agg_status agg_batch_sync(agg_batch* b, uint64_t* n_groups) {
+  if (!b) return AGG_ERR_INVALID_ARG;
+  DeviceGuard g(b->device);
+  if (cudaStreamSynchronize(b->last_stream) != cudaSuccess) {
+    cudaGetLastError();
+    return AGG_ERR_CUDA;
+  }
+  unsigned long long bits = 0;
+  for (uint32_t tm = 0; tm < b->nteams; ++tm) {
+    unsigned long long x = 0;
+    if (cudaMemcpy(&x, &b->ctrl[tm]->status_bits, 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return AGG_ERR_CUDA;
+    }
+    bits |= x;
+  }
+  if (n_groups && b->count &&
+      cudaMemcpy(n_groups, b->d_ngroups, (size_t)b->count * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return AGG_ERR_CUDA;
+  }
+  if (bits) {
+    const agg_status st = status_from_bits(bits);
+    const agg_status r = batch_init_teams(b);  // clear every team's state for the next run
+    return r != AGG_OK ? r : st;
+  }
+  return AGG_OK;
+}
+
+agg_status agg_batch_destroy(agg_batch* b) {
+  if (!b) return AGG_OK;
+  DeviceGuard g(b->device);
+  cudaDeviceSynchronize();
+  cudaGetLastError();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->work) cudaFree(b->work);
+  if (b->staging) cudaFree(b->staging);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_team_off) cudaFree(b->d_team_off);
+  if (b->d_team_items) cudaFree(b->d_team_items);
+  if (b->d_ngroups) cudaFree(b->d_ngroups);
+  delete b;
   return AGG_OK;
 }
 

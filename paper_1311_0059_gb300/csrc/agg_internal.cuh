@@ -116,5 +116,9 @@ struct KernelInfo {
 cudaError_t hash_kernel_info(int ent_kind, int vt, uint32_t ns, int device, KernelInfo* out);
 cudaError_t hash_launch(int ent_kind, int vt, const HashParams& p, const KernelInfo& ki, cudaStream_t s);
 cudaError_t hash_init_table(uint8_t* ent, uint32_t* tags, uint32_t slots, int ent_kind, cudaStream_t s);
+cudaError_t hash_batch_kernel_info(int ent_kind, int vt, uint32_t ns, int device, KernelInfo* out);
+cudaError_t hash_batch_launch(int ent_kind, int vt, const HashParams* items, const uint32_t* team_off,
+                              const uint32_t* team_items, uint32_t team_blocks, uint32_t nteams, size_t smem,
+                              cudaStream_t s);
 
 }  // namespace agg

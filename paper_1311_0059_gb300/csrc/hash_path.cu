@@ -147,16 +147,29 @@ __device__ inline Cache carve_cache(unsigned char* base, uint32_t ns, bool mm) {
 
 // ---------------------------------------------------------------- grid barrier
 
-// Counting grid barrier for a cooperative launch.  The wait is bounded: after
-// timeout_ns the block records AGG_ERR_TIMEOUT and returns false.
-__device__ bool grid_barrier(Ctrl* c, uint64_t timeout_ns, Smem& S) {
+// The blocks that run one group-by together: the whole grid for agg_run, a
+// slice of it for one instance of a batch.  nb == 1 makes every team barrier a
+// __syncthreads.
+struct Team {
+  uint32_t nb;   // blocks in the team
+  uint32_t bid;  // this block's index in the team
+};
+
+// Counting barrier over the team's blocks (co-resident: cooperative launch).
+// The wait is bounded: after timeout_ns the block records AGG_ERR_TIMEOUT and
+// returns false.
+__device__ bool grid_barrier(const Team& T, Ctrl* c, uint64_t timeout_ns, Smem& S) {
+  if (T.nb == 1) {
+    __syncthreads();
+    return true;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t ok = 1;
     const uint32_t g = ld_acquire_u32(&c->bar_gen);
     __threadfence();
     const uint32_t arrived = atomicAdd(&c->bar_count, 1u) + 1u;
-    if (arrived == gridDim.x) {
+    if (arrived == T.nb) {
       atomicExch(&c->bar_count, 0u);
       __threadfence();
       atomicAdd(&c->bar_gen, 1u);
@@ -181,11 +194,11 @@ __device__ bool grid_barrier(Ctrl* c, uint64_t timeout_ns, Smem& S) {
 // Phase timer of block 0 (diagnostics, reported by agg_get_stats).
 struct Timer {
   uint64_t t;
-  __device__ void start() {
-    if (blockIdx.x == 0 && threadIdx.x == 0) t = globaltimer();
+  __device__ void start(const Team& T) {
+    if (T.bid == 0 && threadIdx.x == 0) t = globaltimer();
   }
-  __device__ void lap(Ctrl* c, int phase) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+  __device__ void lap(const Team& T, Ctrl* c, int phase) {
+    if (T.bid == 0 && threadIdx.x == 0) {
       const uint64_t now = globaltimer();
       c->phase_ns[phase] += now - t;
       t = now;
@@ -671,11 +684,11 @@ __device__ void emit_one(const HashParams& P, uint8_t* e, unsigned long long pos
 // Writes every occupied slot of the active table (and the side slot) to the
 // output and resets them.
 template <int ENT>
-__device__ void emit_table(const HashParams& P, uint32_t s_act, uint32_t level, Smem& S) {
+__device__ void emit_table(const HashParams& P, const Team& T, uint32_t s_act, uint32_t level, Smem& S) {
   const uint32_t words = s_act / 4;
   constexpr uint32_t WPT = 4;  // tag words per thread
   const uint32_t seg_words = THREADS * WPT;
-  for (uint32_t seg = blockIdx.x; (uint64_t)seg * seg_words < words; seg += gridDim.x) {
+  for (uint32_t seg = T.bid; (uint64_t)seg * seg_words < words; seg += T.nb) {
     const uint32_t w0 = seg * seg_words + threadIdx.x * WPT;
     uint32_t tw[WPT];
     uint32_t oc = 0;
@@ -713,7 +726,7 @@ __device__ void emit_table(const HashParams& P, uint32_t s_act, uint32_t level, 
     __syncthreads();
   }
   // the side slot of the empty-marker key
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+  if (T.bid == T.nb - 1 && threadIdx.x == 0) {
     uint8_t* tb = reinterpret_cast<uint8_t*>(P.tags) + P.slots;
     if (__ldcg(tb)) {
       const unsigned long long pos = atomicAdd(&P.ctrl->out_count, 1ull);
@@ -843,7 +856,8 @@ __device__ __forceinline__ bool load_chunk_record(const HashParams& P, uint32_t 
 // the level's global table G (or spill further).  Two grid barriers per round;
 // pass C needs none before the next round's pass A.
 template <int ENT>
-__device__ bool smem_round(const HashParams& P, const Level& G, Smem& S, const Cache& cc, uint32_t src, uint32_t c0,
+__device__ bool smem_round(const HashParams& P, const Team& T, const Level& G, Smem& S, const Cache& cc, uint32_t src,
+                           uint32_t c0,
                            uint32_t c1, uint64_t tot, uint32_t par, longlong2* scratch) {
   Ctrl* C = P.ctrl;
   const uint32_t* dcount = P.dir_count[src];
@@ -867,7 +881,7 @@ __device__ bool smem_round(const HashParams& P, const Level& G, Smem& S, const C
   // ---- pass A: records per sub-partition
   for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) hist[i] = 0;
   __syncthreads();
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (uint64_t t = T.bid; t < ntiles; t += T.nb) {
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       long long k, v;
@@ -878,7 +892,7 @@ __device__ bool smem_round(const HashParams& P, const Level& G, Smem& S, const C
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < nsub; i += THREADS)
     if (hist[i]) atomicAdd(&C->sub_tot[par][i], hist[i]);
-  if (!grid_barrier(C, P.timeout_ns, S)) return false;
+  if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
 
   // ---- pass B: offsets, then scatter into scratch grouped by sub-partition
   {
@@ -892,16 +906,16 @@ __device__ bool smem_round(const HashParams& P, const Level& G, Smem& S, const C
     for (uint32_t i = 0; i < per; ++i) {
       if (s0 + i >= nsub) break;
       base[s0 + i] = acc;
-      if (blockIdx.x == 0) C->sub_base[par][s0 + i] = acc;
+      if (T.bid == 0) C->sub_base[par][s0 + i] = acc;
       acc += __ldcg(&C->sub_tot[par][s0 + i]);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) C->sub_base[par][nsub] = total;
+    if (T.bid == 0 && threadIdx.x == 0) C->sub_base[par][nsub] = total;
     for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) tcnt[i] = 0;
     __syncthreads();
   }
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    if (threadIdx.x == 0 && t + gridDim.x < ntiles) {
-      const uint32_t nc = __ldcg(list + c0 + (uint32_t)(t + gridDim.x));
+  for (uint64_t t = T.bid; t < ntiles; t += T.nb) {
+    if (threadIdx.x == 0 && t + T.nb < ntiles) {
+      const uint32_t nc = __ldcg(list + c0 + (uint32_t)(t + T.nb));
       prefetch_l2(P.stg[src] + (size_t)nc * CH * REC_BYTES, __ldcg(dcount + nc) * (uint32_t)REC_BYTES);
     }
     long long k[RPT], v[RPT];
@@ -942,18 +956,18 @@ __device__ bool smem_round(const HashParams& P, const Level& G, Smem& S, const C
     for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) tcnt[i] = 0;
     __syncthreads();
   }
-  if (!grid_barrier(C, P.timeout_ns, S)) return false;
+  if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
 
   // ---- pass C: whole sub-partitions aggregated in shared memory
   cache_reset_all(cc, S, Ent<ENT>::MM);
-  if (blockIdx.x == 0)  // counters of this parity are next used two rounds on
+  if (T.bid == 0)  // counters of this parity are next used two rounds on
     for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) {
       C->sub_tot[par][i] = 0;
       C->sub_cur[par][i] = 0;
     }
   __syncthreads();
   unsigned long long my_recs = 0, my_groups = 0;
-  for (uint32_t sbi = blockIdx.x; sbi < nsub; sbi += gridDim.x) {
+  for (uint32_t sbi = T.bid; sbi < nsub; sbi += T.nb) {
     uint32_t lo = __ldcg(&C->sub_base[par][sbi]), hi = __ldcg(&C->sub_base[par][sbi + 1]);
     if (hi > tot || lo > hi) {  // inconsistent offsets: report, never read past the scratch
       if (threadIdx.x == 0) set_status(C, AGG_ERR_INTERNAL);
@@ -995,21 +1009,21 @@ __device__ bool smem_round(const HashParams& P, const Level& G, Smem& S, const C
 
 // Restores the entries that served as scratch to the empty state.
 template <int ENT>
-__device__ void restore_scratch(const HashParams& P, uint32_t half) {
-  for (uint64_t s = half + blockIdx.x * (uint64_t)THREADS + threadIdx.x; s < P.slots;
-       s += (uint64_t)gridDim.x * THREADS)
+__device__ void restore_scratch(const HashParams& P, const Team& T, uint32_t half) {
+  for (uint64_t s = half + T.bid * (uint64_t)THREADS + threadIdx.x; s < P.slots;
+       s += (uint64_t)T.nb * THREADS)
     Ent<ENT>::reset(Ent<ENT>::at(P.ent, (uint32_t)s));
 }
 
 // Last block to arrive publishes the group count and the run's statistics,
 // then zeroes the per-run control fields for the next run.
-__device__ void final_step(const HashParams& P, uint32_t levels) {
+__device__ void final_step(const HashParams& P, const Team& T, uint32_t levels) {
   __syncthreads();
   if (threadIdx.x != 0) return;
   Ctrl* C = P.ctrl;
   __threadfence();
   const uint32_t prev = atomicAdd(&C->done_count, 1u);
-  if (prev != gridDim.x - 1) return;
+  if (prev != T.nb - 1) return;
   __threadfence();
   volatile Ctrl* V = C;
   const unsigned long long ng = V->out_count;
@@ -1050,16 +1064,16 @@ enum Phase { PH_L0 = 0, PH_L0_WAIT, PH_L0_EMIT, PH_LISTS, PH_ROUND_AGG, PH_ROUND
 
 // ---------------------------------------------------------------- the kernel
 
+// The whole group-by of one input by one team: level 0 over the input, then
+// the spilled levels.  Returns false when a bounded wait gave up (the team
+// must stop).
 template <int ENT, int VT>
-__global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashParams P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
-  const Cache cc = carve_cache(smem_raw + ((sizeof(Smem) + 15) & ~size_t(15)), P.ns, Ent<ENT>::MM);
+__device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const Cache& cc) {
   Ctrl* C = P.ctrl;
   const uint32_t fan = 1u << P.fan_log2;
   Timer tm, total;
-  tm.start();
-  total.start();
+  tm.start(T);
+  total.start(T);
 
   for (uint32_t p = threadIdx.x; p < MAX_FAN; p += THREADS) {
     S.cnt[p] = 0;
@@ -1096,10 +1110,10 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
     L.dst = 0;
     L.fan_mask = fan - 1;
     const uint64_t ntiles = (P.n + TILE - 1) / TILE;
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (uint64_t t = T.bid; t < ntiles; t += T.nb) {
       const uint64_t row0 = t * TILE;
-      if (threadIdx.x == 0 && P.vec_ok && t + gridDim.x < ntiles) {  // stage this block's next tile in L2
-        const uint64_t nr0 = (t + gridDim.x) * TILE;
+      if (threadIdx.x == 0 && P.vec_ok && t + T.nb < ntiles) {  // stage this block's next tile in L2
+        const uint64_t nr0 = (t + T.nb) * TILE;
         const uint64_t nrows = P.n - nr0 < (uint64_t)TILE ? P.n - nr0 : (uint64_t)TILE;
         prefetch_l2(P.keys + nr0, (uint32_t)(nrows * 8));
         if (P.has_vals)
@@ -1150,27 +1164,27 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
     }
     cache_flush<ENT>(P, cc, S);
     finalize_chunks(P, S, 0, 0);
-    tm.lap(C, PH_L0);
-    if (!grid_barrier(C, P.timeout_ns, S)) return;
-    tm.lap(C, PH_L0_WAIT);
+    tm.lap(T, C, PH_L0);
+    if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+    tm.lap(T, C, PH_L0_WAIT);
     const unsigned long long spilled = ld_relaxed_u64(&C->pool_next[0]);
-    emit_table<ENT>(P, L.s_act, 0, S);
-    tm.lap(C, PH_L0_EMIT);
+    emit_table<ENT>(P, T, L.s_act, 0, S);
+    tm.lap(T, C, PH_L0_EMIT);
     if (spilled == 0) {
-      total.lap(C, PH_TOTAL);
-      final_step(P, 1);
-      return;
+      total.lap(T, C, PH_TOTAL);
+      final_step(P, T, 1);
+      return true;
     }
-    if (!grid_barrier(C, P.timeout_ns, S)) return;
-    tm.lap(C, PH_ROUND_WAIT);
+    if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+    tm.lap(T, C, PH_ROUND_WAIT);
   }
 
   // ================= levels 1..: recursive processing of spilled partitions
   for (uint32_t level = 1;; ++level) {
     if (level >= AGG_MAX_LEVELS) {
-      if (threadIdx.x == 0 && blockIdx.x == 0) set_status(C, AGG_ERR_INTERNAL);
-      final_step(P, level);
-      return;
+      if (threadIdx.x == 0 && T.bid == 0) set_status(C, AGG_ERR_INTERNAL);
+      final_step(P, T, level);
+      return true;
     }
     const uint32_t src = (level + 1) & 1, dst = level & 1, set = level & 1;
     uint32_t* dpart = P.dir_part[src];
@@ -1179,7 +1193,7 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
     // P1: per-partition chunk and record counts of the source area.  Block 0
     // also clears the level's round counters here, before the level's first
     // barrier, so every block later reads the same values.
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (threadIdx.x == 0 && T.bid == 0) {
       C->pool_next[dst] = 0;
       C->overflow_used[level & 1] = 0;
       C->lvl_sub_records[0] = C->lvl_sub_records[1] = 0;
@@ -1193,8 +1207,8 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
       S.hrec[p] = 0;
     }
     __syncthreads();
-    for (unsigned long long c = blockIdx.x * (unsigned long long)THREADS + threadIdx.x; c < nch;
-         c += (unsigned long long)gridDim.x * THREADS) {
+    for (unsigned long long c = T.bid * (unsigned long long)THREADS + threadIdx.x; c < nch;
+         c += (unsigned long long)T.nb * THREADS) {
       const uint32_t p = __ldcg(dpart + c);
       atomicAdd(&S.cnt[p], 1u);
       atomicAdd(&S.hrec[p], (unsigned long long)__ldcg(dcount + c));
@@ -1207,7 +1221,7 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
       }
       S.cnt[p] = 0;
     }
-    if (!grid_barrier(C, P.timeout_ns, S)) return;
+    if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
     // P3: chunk lists grouped by partition
     if (threadIdx.x == 0) {
       uint32_t acc = 0;
@@ -1218,21 +1232,21 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
       S.begin[fan] = acc;
     }
     __syncthreads();
-    for (unsigned long long c = blockIdx.x * (unsigned long long)THREADS + threadIdx.x; c < nch;
-         c += (unsigned long long)gridDim.x * THREADS) {
+    for (unsigned long long c = T.bid * (unsigned long long)THREADS + threadIdx.x; c < nch;
+         c += (unsigned long long)T.nb * THREADS) {
       const uint32_t p = __ldcg(dpart + c);
       const uint32_t at = atomicAdd(&C->part_cursor[set][p], 1u);
       list[S.begin[p] + at] = (uint32_t)c;
     }
-    if (!grid_barrier(C, P.timeout_ns, S)) return;
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+    if (threadIdx.x == 0 && T.bid == 0) {
       for (uint32_t p = 0; p < MAX_FAN; ++p) {
         C->part_records[set ^ 1][p] = 0;
         C->part_chunks[set ^ 1][p] = 0;
         C->part_cursor[set ^ 1][p] = 0;
       }
     }
-    tm.lap(C, PH_LISTS);
+    tm.lap(T, C, PH_LISTS);
     // Rounds.  At levels >= 1 the global table keeps the lower half of the
     // slots (keys that overflow shared memory, partitions too big for a
     // shared-memory round) and the upper half of the entry memory serves as
@@ -1262,20 +1276,20 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
           tot += r;
           ++q;
         }
-        if (!smem_round<ENT>(P, G, S, cc, src, S.begin[p], S.begin[q], tot, rnd & 1, scratch)) return;
-        if (threadIdx.x == 0 && blockIdx.x == 0) C->rounds += 1;
+        if (!smem_round<ENT>(P, T, G, S, cc, src, S.begin[p], S.begin[q], tot, rnd & 1, scratch)) return false;
+        if (threadIdx.x == 0 && T.bid == 0) C->rounds += 1;
         ++rnd;
-        tm.lap(C, PH_ROUND_AGG);
+        tm.lap(T, C, PH_ROUND_AGG);
         p = q;
         continue;
       }
       // a partition too big for a shared-memory round: global-table round
       const uint32_t c0 = S.begin[p], c1 = S.begin[q];
       const uint64_t ntiles = c1 - c0;
-      if (!grid_barrier(C, P.timeout_ns, S)) return;  // shared-memory rounds before it are complete
-      for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        if (threadIdx.x == 0 && t + gridDim.x < ntiles) {  // one tile is one chunk (CH == TILE)
-          const uint32_t nc = __ldcg(list + c0 + (uint32_t)(t + gridDim.x));
+      if (!grid_barrier(T, C, P.timeout_ns, S)) return false;  // shared-memory rounds before it are complete
+      for (uint64_t t = T.bid; t < ntiles; t += T.nb) {
+        if (threadIdx.x == 0 && t + T.nb < ntiles) {  // one tile is one chunk (CH == TILE)
+          const uint32_t nc = __ldcg(list + c0 + (uint32_t)(t + T.nb));
           prefetch_l2(P.stg[src] + (size_t)nc * CH * REC_BYTES, __ldcg(dcount + nc) * (uint32_t)REC_BYTES);
         }
         adapt_begin_tile(S, cc.n != 0 && P.cache != 0, P.dedup != 0);
@@ -1292,27 +1306,57 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
         adapt_end_tile(S, cc.n != 0 && P.cache != 0, P.dedup != 0);
       }
       cache_flush<ENT>(P, cc, S);
-      tm.lap(C, PH_ROUND_AGG);
-      if (!grid_barrier(C, P.timeout_ns, S)) return;
-      tm.lap(C, PH_ROUND_WAIT);
-      emit_table<ENT>(P, half, level, S);
-      if (threadIdx.x == 0 && blockIdx.x == 0) C->rounds += 1;
-      tm.lap(C, PH_ROUND_EMIT);
-      if (!grid_barrier(C, P.timeout_ns, S)) return;
-      tm.lap(C, PH_ROUND_WAIT);
+      tm.lap(T, C, PH_ROUND_AGG);
+      if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+      tm.lap(T, C, PH_ROUND_WAIT);
+      emit_table<ENT>(P, T, half, level, S);
+      if (threadIdx.x == 0 && T.bid == 0) C->rounds += 1;
+      tm.lap(T, C, PH_ROUND_EMIT);
+      if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+      tm.lap(T, C, PH_ROUND_WAIT);
       p = q;
     }
     finalize_chunks(P, S, dst, level);
-    if (!grid_barrier(C, P.timeout_ns, S)) return;
-    tm.lap(C, PH_ROUND_WAIT);
-    if (ld_acquire_u32(&C->overflow_used[level & 1])) emit_table<ENT>(P, half, level, S);
-    tm.lap(C, PH_ROUND_EMIT);
+    if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+    tm.lap(T, C, PH_ROUND_WAIT);
+    if (ld_acquire_u32(&C->overflow_used[level & 1])) emit_table<ENT>(P, T, half, level, S);
+    tm.lap(T, C, PH_ROUND_EMIT);
     if (ld_relaxed_u64(&C->pool_next[dst]) == 0) {
-      restore_scratch<ENT>(P, half);
-      total.lap(C, PH_TOTAL);
-      final_step(P, level + 1);
-      return;
+      restore_scratch<ENT>(P, T, half);
+      total.lap(T, C, PH_TOTAL);
+      final_step(P, T, level + 1);
+      return true;
     }
+  }
+}
+
+template <int ENT, int VT>
+__global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  const Cache cc = carve_cache(smem_raw + ((sizeof(Smem) + 15) & ~size_t(15)), P.ns, Ent<ENT>::MM);
+  const Team T{gridDim.x, blockIdx.x};
+  run_groupby<ENT, VT>(P, T, S, cc);
+}
+
+// Batched group-by: teams of `team_blocks` consecutive blocks; team t runs the
+// instances team_items[team_off[t] .. team_off[t+1]) one after another, each
+// with the whole algorithm of run_groupby.  A team barrier between instances
+// keeps a block from starting the next instance while another block of the
+// team still finishes the previous one.
+template <int ENT, int VT>
+__global__ void __launch_bounds__(THREADS, 2)
+    hash_batch_kernel(const HashParams* __restrict__ items, const uint32_t* __restrict__ team_off,
+                      const uint32_t* __restrict__ team_items, uint32_t team_blocks) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  const uint32_t team = blockIdx.x / team_blocks;
+  const Team T{team_blocks, blockIdx.x % team_blocks};
+  for (uint32_t j = team_off[team]; j < team_off[team + 1]; ++j) {
+    const HashParams& P = items[team_items[j]];
+    const Cache cc = carve_cache(smem_raw + ((sizeof(Smem) + 15) & ~size_t(15)), P.ns, Ent<ENT>::MM);
+    if (!run_groupby<ENT, VT>(P, T, S, cc)) return;
+    if (!grid_barrier(T, P.ctrl, P.timeout_ns, S)) return;
   }
 }
 
@@ -1330,6 +1374,21 @@ __global__ void init_table_kernel(uint8_t* ent, uint32_t* tags, uint32_t slots) 
 template <int ENT, int VT>
 void* kernel_ptr() {
   return reinterpret_cast<void*>(&hash_groupby_kernel<ENT, VT>);
+}
+
+template <int ENT, int VT>
+void* batch_kernel_ptr() {
+  return reinterpret_cast<void*>(&hash_batch_kernel<ENT, VT>);
+}
+
+void* pick_batch_kernel(int ent, int vt) {
+  if (vt == AGG_I32) {
+    if (ent == ENT32_CS) return batch_kernel_ptr<ENT32_CS, AGG_I32>();
+    if (ent == ENT32_CSMM32) return batch_kernel_ptr<ENT32_CSMM32, AGG_I32>();
+    return batch_kernel_ptr<ENT64, AGG_I32>();
+  }
+  if (ent == ENT32_CS) return batch_kernel_ptr<ENT32_CS, AGG_I64>();
+  return batch_kernel_ptr<ENT64, AGG_I64>();
 }
 
 void* pick_kernel(int ent, int vt) {
@@ -1362,6 +1421,31 @@ cudaError_t hash_kernel_info(int ent_kind, int vt, uint32_t ns, int device, Kern
   out->blocks = per_sm * sms;
   out->smem = smem;
   return cudaSuccess;
+}
+
+cudaError_t hash_batch_kernel_info(int ent_kind, int vt, uint32_t ns, int device, KernelInfo* out) {
+  void* k = pick_batch_kernel(ent_kind, vt);
+  const size_t smem = smem_bytes(ent_kind, ns);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, THREADS, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  out->blocks = per_sm * sms;
+  out->smem = smem;
+  return cudaSuccess;
+}
+
+cudaError_t hash_batch_launch(int ent_kind, int vt, const HashParams* items, const uint32_t* team_off,
+                              const uint32_t* team_items, uint32_t team_blocks, uint32_t nteams, size_t smem,
+                              cudaStream_t s) {
+  void* k = pick_batch_kernel(ent_kind, vt);
+  void* args[] = {const_cast<HashParams**>(&items), const_cast<uint32_t**>(&team_off),
+                  const_cast<uint32_t**>(&team_items), &team_blocks};
+  return cudaLaunchCooperativeKernel(k, dim3(nteams * team_blocks), dim3(THREADS), args, smem, s);
 }
 
 cudaError_t hash_launch(int ent_kind, int vt, const HashParams& p, const KernelInfo& ki, cudaStream_t s) {

@@ -9,7 +9,8 @@ import torch
 
 from . import _abi
 from ._abi import (AGG_COUNT, AGG_I32, AGG_I64, AGG_MAX, AGG_MIN, AGG_PATH_HASH, AGG_PATH_SORT, AGG_SUM,
-                   agg_output, agg_plan_info, agg_spec, agg_stats, agg_tuning, check)
+                   agg_batch_item, agg_batch_tuning, agg_output, agg_plan_info, agg_spec, agg_stats, agg_tuning,
+                   check)
 
 ALL_OPS = AGG_COUNT | AGG_SUM | AGG_MIN | AGG_MAX
 
@@ -147,3 +148,55 @@ class GroupBy:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Many independent group-bys run by one persistent launch (agg_batch_*).
+
+    `instances` is a list of (keys, vals, budget_bytes, expected_groups) with
+    device tensors; outputs are allocated here, one Output per instance."""
+
+    def __init__(self, instances, ops: int = ALL_OPS, value_type: int = AGG_I64, seed: int = 0,
+                 tuning: agg_batch_tuning | None = None, capacities=None):
+        self.lib = _abi.load()
+        self.spec = make_spec(ops, value_type, AGG_PATH_HASH, 0, seed)
+        self.ops = ops
+        self.outs = []
+        items = (agg_batch_item * max(len(instances), 1))()
+        for i, (k, v, budget, eg) in enumerate(instances):
+            cap = k.numel() if capacities is None else capacities[i]
+            o = Output(cap, ops, k.device)
+            self.outs.append(o)
+            items[i] = agg_batch_item(d_keys=k.data_ptr(), d_vals=v.data_ptr() if v is not None else None,
+                                      n=k.numel(), budget=budget, expected_groups=eg, out=o.abi)
+        self.inputs = instances
+        h = ctypes.c_void_p()
+        check(self.lib.agg_batch_create(ctypes.byref(self.spec), items, len(instances),
+                                        ctypes.byref(tuning) if tuning is not None else None, ctypes.byref(h)),
+              "agg_batch_create")
+        self.h = h
+        self.count = len(instances)
+
+    def run_async(self, stream=None) -> int:
+        return self.lib.agg_batch_run(self.h, _stream_ptr(stream))
+
+    def sync(self):
+        ng = (ctypes.c_uint64 * max(self.count, 1))()
+        check(self.lib.agg_batch_sync(self.h, ng), "agg_batch_sync")
+        return [ng[i] for i in range(self.count)]
+
+    def run(self, stream=None):
+        check(self.run_async(stream), "agg_batch_run")
+        ng = self.sync()
+        return [o.result(g) for o, g in zip(self.outs, ng)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.agg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
