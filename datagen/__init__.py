@@ -130,11 +130,29 @@ def uniform_ranks(seed: int, domain: int, start: int, count: int) -> np.ndarray:
     return mulhi_u32(stream(seed, STREAM_KEY, start, count), domain)
 
 
+_HARMONIC = np.zeros(0)
+
+
+def harmonic(n: int) -> np.ndarray:
+    """Partial sums H[r-1] = 1 + 1/2 + ... + 1/r for r = 1..n, float64, summed in
+    order; one growing master table, so every prefix has the same bytes."""
+    global _HARMONIC
+    if _HARMONIC.size < n:
+        size = max(n, 2 * _HARMONIC.size)
+        _HARMONIC = np.cumsum(1.0 / np.arange(1, size + 1, dtype=np.float64))
+    return _HARMONIC[:n]
+
+
 def zipf_cdf(domain: int, s: float) -> np.ndarray:
-    """Float64 CDF table of Zipf(s) over ``domain`` ranks; last entry 2.0."""
-    w = np.arange(1, domain + 1, dtype=np.float64) ** (-float(s))
-    cdf = np.cumsum(w)
-    cdf /= cdf[-1]
+    """Float64 CDF table of Zipf(s) over ``domain`` ranks; last entry 2.0.
+    For s = 1 the table is the harmonic prefix divided by its last entry."""
+    if float(s) == 1.0:
+        h = harmonic(domain)
+        cdf = h / h[-1]
+    else:
+        w = np.arange(1, domain + 1, dtype=np.float64) ** (-float(s))
+        cdf = np.cumsum(w)
+        cdf /= cdf[-1]
     cdf[-1] = 2.0
     return cdf
 
@@ -265,4 +283,33 @@ def batch_workloads(count: int = 4096, seed: int = 0, rows=(1_000, 4_000_000), c
         b = int(np.exp(np.log(budget[0]) + u[i, 4] * (np.log(budget[1]) - np.log(budget[0]))))
         out.append(Workload(f"batch instance {i}", n=n, domain=dom, dist="zipf" if zipf else "uniform",
                             zipf_s=float(s), vtype="i64_2p20", seed=instance_seed(seed, i), budget=b, ops=15))
+    return out
+
+
+STREAM_ARRIVALS = 5
+
+
+def served_workloads(duration: float = 60.0, rate: float = 200.0, seed: int = 0, rows=(10_000, 100_000_000),
+                     card=(0.001, 0.50), budget=(16 << 20, 2 << 30)):
+    """The served workload: queries arriving as a Poisson process of `rate` per
+    second over `duration` seconds (exponential gaps from stream 5).  Per query
+    (five draws of stream 4): rows log-uniform in `rows`, distinct keys a
+    uniform fraction `card` of the rows, uniform or Zipf(1.0) keys (1/2 each),
+    int64 values in [0, 2**20), budget log-uniform in `budget`.
+    Returns [(arrival_seconds, Workload)]."""
+    expect = int(duration * rate * 1.5) + 64
+    gaps = -np.log1p(-unit_doubles(seed, STREAM_ARRIVALS, expect)) / rate
+    t = np.cumsum(gaps)
+    count = int(np.searchsorted(t, duration))
+    u = unit_doubles(seed + 1, STREAM_PARAMS, 5 * max(count, 1)).reshape(-1, 5)
+    out = []
+    for i in range(count):
+        n = int(np.exp(np.log(rows[0]) + u[i, 0] * (np.log(rows[1]) - np.log(rows[0]))))
+        frac = card[0] + u[i, 1] * (card[1] - card[0])
+        dom = max(1, int(round(frac * n)))
+        zipf = u[i, 2] < 0.5
+        b = int(np.exp(np.log(budget[0]) + u[i, 4] * (np.log(budget[1]) - np.log(budget[0]))))
+        out.append((float(t[i]), Workload(f"query {i}", n=n, domain=dom, dist="zipf" if zipf else "uniform",
+                                          zipf_s=1.0, vtype="i64_2p20", seed=instance_seed(seed + 1, i), budget=b,
+                                          ops=15)))
     return out

@@ -236,6 +236,67 @@ agg_status agg_batch_sync(agg_batch* b, uint64_t* n_groups);
 /* Releases the batch (waits for its work first).  NULL is allowed. */
 agg_status agg_batch_destroy(agg_batch* b);
 
+/* ---- Served form: queries arrive over time and share the device ---- */
+
+/* One query submitted to a server: input, declared budget and output (device
+ * pointers, caller-owned, valid until the query completes).  If `ready` is a
+ * cudaEvent_t (may be NULL), the query's work waits for it (for example the
+ * event recorded after the input was produced). */
+typedef struct agg_query {
+  const int64_t* d_keys;
+  const void* d_vals;
+  uint64_t n;
+  size_t budget;            /* declared working-memory budget, >= AGG_MIN_BUDGET */
+  uint64_t expected_groups; /* optional */
+  agg_output out;           /* out.d_n_groups is ignored: see agg_server_poll */
+  void* ready;
+} agg_query;
+
+enum { AGG_QUERY_QUEUED = 0, AGG_QUERY_RUNNING = 1, AGG_QUERY_DONE = 2, AGG_QUERY_FAILED = 3 };
+
+typedef struct agg_query_info {
+  int32_t state;        /* AGG_QUERY_* */
+  int32_t status;       /* agg_status of a finished query */
+  uint64_t n_groups;
+  double t_submit;      /* host steady-clock seconds */
+  double t_start;       /* admitted and launched */
+  double t_done;        /* completion observed by agg_server_progress */
+  uint32_t team_blocks; /* thread blocks that ran it */
+  uint32_t pad;
+} agg_query_info;
+
+typedef struct agg_server_stats {
+  uint64_t submitted, completed, running, queued;
+  uint64_t pool_bytes, pool_in_use, pool_peak;  /* working memory of admitted queries */
+  uint64_t max_concurrent;                      /* most queries running at once */
+} agg_server_stats;
+
+typedef struct agg_server agg_server;
+
+/* Creates a server with a device memory pool of pool_bytes for the working
+ * memory of its queries (their declared budgets, the multi-user memory
+ * constraint of Section 3.2) and at most max_active queries running at once.
+ * spec.ops and spec.value_type apply to every query. */
+agg_status agg_server_create(const agg_spec* spec, size_t pool_bytes, uint32_t max_active, agg_server** out);
+
+/* Queues a query (never blocks, never launches).  *ticket identifies it. */
+agg_status agg_server_submit(agg_server* s, const agg_query* q, uint64_t* ticket);
+
+/* One turn of the request loop: notices finished queries (freeing their budget
+ * and slot), then admits queued queries in arrival order while a slot is free
+ * and the next query's budget fits the free pool, each launched at once on its
+ * slot's stream so that admitted queries run concurrently.  Non-blocking.
+ * *completed (may be NULL) receives the number of queries finished now. */
+agg_status agg_server_progress(agg_server* s, uint32_t* completed);
+
+/* State, result size and timestamps of a query. */
+agg_status agg_server_poll(agg_server* s, uint64_t ticket, agg_query_info* info);
+
+agg_status agg_server_get_stats(agg_server* s, agg_server_stats* st);
+
+/* Waits for every running query, then releases the server. */
+agg_status agg_server_destroy(agg_server* s);
+
 /* Size of the fixed working memory of agg_run_noalloc. */
 #define AGG_NOALLOC_SLOTS (1u << 18)
 #define AGG_NOALLOC_MAX_ROWS ((uint64_t)AGG_NOALLOC_SLOTS / 4)

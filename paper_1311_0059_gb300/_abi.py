@@ -81,6 +81,25 @@ class agg_batch_tuning(ctypes.Structure):
                 ("max_load_factor", ctypes.c_double), ("fan_out", ctypes.c_uint32), ("use_graph", ctypes.c_uint32)]
 
 
+class agg_query(ctypes.Structure):
+    _fields_ = [("d_keys", _P), ("d_vals", _P), ("n", _U64), ("budget", ctypes.c_size_t),
+                ("expected_groups", _U64), ("out", agg_output), ("ready", _P)]
+
+
+class agg_query_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("n_groups", _U64), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double), ("team_blocks", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
+
+
+class agg_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", _U64), ("completed", _U64), ("running", _U64), ("queued", _U64),
+                ("pool_bytes", _U64), ("pool_in_use", _U64), ("pool_peak", _U64), ("max_concurrent", _U64)]
+
+
+AGG_QUERY_QUEUED, AGG_QUERY_RUNNING, AGG_QUERY_DONE, AGG_QUERY_FAILED = 0, 1, 2, 3
+
+
 # name -> (restype, argtypes); the names are exactly those declared in include/agg.h
 SIGNATURES = {
     "agg_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(agg_spec), ctypes.POINTER(_P)]),
@@ -101,6 +120,13 @@ SIGNATURES = {
     "agg_batch_run": (ctypes.c_int, [_P, _P]),
     "agg_batch_sync": (ctypes.c_int, [_P, ctypes.POINTER(_U64)]),
     "agg_batch_destroy": (ctypes.c_int, [_P]),
+    "agg_server_create": (ctypes.c_int, [ctypes.POINTER(agg_spec), ctypes.c_size_t, ctypes.c_uint32,
+                                         ctypes.POINTER(_P)]),
+    "agg_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(agg_query), ctypes.POINTER(_U64)]),
+    "agg_server_progress": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32)]),
+    "agg_server_poll": (ctypes.c_int, [_P, _U64, ctypes.POINTER(agg_query_info)]),
+    "agg_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(agg_server_stats)]),
+    "agg_server_destroy": (ctypes.c_int, [_P]),
 }
 
 AGG_NOALLOC_SLOTS = 1 << 18

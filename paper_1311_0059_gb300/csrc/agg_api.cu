@@ -4,7 +4,11 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <chrono>
+#include <deque>
+#include <map>
 #include <new>
+#include <unordered_map>
 #include <queue>
 #include <vector>
 
@@ -920,6 +924,338 @@ agg_status agg_batch_destroy(agg_batch* b) {
   if (b->d_team_items) cudaFree(b->d_team_items);
   if (b->d_ngroups) cudaFree(b->d_ngroups);
   delete b;
+  return AGG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- served form
+
+struct ServerQuery {
+  agg_query q{};
+  agg_query_info info{};
+  uint64_t pool_off = 0, pool_len = 0;
+  int slot = -1;
+};
+
+struct agg_server {
+  int device = 0;
+  agg_spec spec{};
+  int ent_kind = 0;
+  uint32_t es = 32;
+  agg_tuning tune{};
+  KernelInfo ki{};  // launch shape of one block team (smem) and the whole-GPU block count
+  uint8_t* pool = nullptr;
+  uint64_t pool_bytes = 0, in_use = 0, peak = 0;
+  std::map<uint64_t, uint64_t> free_list;  // offset -> length
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  std::vector<int64_t> slot_ticket;  // -1 = free
+  unsigned long long* pinned = nullptr;  // per slot: status bits, group count
+  std::deque<uint64_t> waiting;
+  std::unordered_map<uint64_t, ServerQuery> queries;
+  uint64_t next_ticket = 1;
+  uint64_t submitted = 0, completed = 0, running = 0, max_conc = 0;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+namespace {
+
+bool pool_alloc(agg_server* s, uint64_t len, uint64_t* off) {
+  len = align_up(len, 256);
+  for (auto it = s->free_list.begin(); it != s->free_list.end(); ++it) {
+    if (it->second < len) continue;
+    *off = it->first;
+    const uint64_t rest = it->second - len, roff = it->first + len;
+    s->free_list.erase(it);
+    if (rest) s->free_list[roff] = rest;
+    s->in_use += len;
+    s->peak = std::max(s->peak, s->in_use);
+    return true;
+  }
+  return false;
+}
+
+void pool_free(agg_server* s, uint64_t off, uint64_t len) {
+  len = align_up(len, 256);
+  s->in_use -= len;
+  auto it = s->free_list.emplace(off, len).first;
+  auto nx = std::next(it);
+  if (nx != s->free_list.end() && it->first + it->second == nx->first) {  // merge with the next
+    it->second += nx->second;
+    s->free_list.erase(nx);
+  }
+  if (it != s->free_list.begin()) {  // merge with the previous
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      s->free_list.erase(it);
+    }
+  }
+}
+
+// Thread blocks of a query's team: more rows, more blocks (power of two, at
+// most half the GPU so that other queries keep running beside it).
+uint32_t team_for(uint64_t n, uint32_t all_blocks) {
+  uint32_t b = 8;
+  while (b < all_blocks / 2 && (uint64_t)b * (1ull << 18) < n) b <<= 1;
+  return std::min(b, std::max(1u, all_blocks / 2));
+}
+
+agg_status server_launch(agg_server* s, ServerQuery& sq, int slot) {
+  cudaStream_t st = s->streams[slot];
+  const agg_query& q = sq.q;
+  Layout L;
+  layout_for(q.budget, s->es, &L);
+  uint8_t* base = s->pool + sq.pool_off;
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(base);
+  uint32_t* tags = reinterpret_cast<uint32_t*>(base + L.tags_off);
+  uint8_t* ent = base + L.ent_off;
+  const uint64_t n = q.n;
+  uint64_t need = (uint64_t)((double)(n ? n : 1) / s->tune.max_load_factor) + BUCKET;
+  need = std::max<uint64_t>((need + BUCKET - 1) / BUCKET * BUCKET, 2 * MIN_SLOTS);
+  const uint64_t slots = std::min<uint64_t>(L.slots, need);
+  const bool may_spill = n > (uint64_t)(0.5 * (double)slots);
+  agg_spec si = s->spec;
+  si.expected_groups = q.expected_groups;
+  const uint32_t fan = plan_fan(&si, s->tune, n, q.budget, s->es);
+  const uint32_t team = team_for(n, (uint32_t)s->ki.blocks);
+  if (q.ready && cudaStreamWaitEvent(st, static_cast<cudaEvent_t>(q.ready), 0) != cudaSuccess) return AGG_ERR_CUDA;
+  if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st) != cudaSuccess ||
+      hash_init_table(ent, tags, (uint32_t)slots, s->ent_kind, st) != cudaSuccess)
+    return AGG_ERR_CUDA;
+  HashParams p{};
+  void* stg = nullptr;
+  uint64_t chunks = 0, data = 0, meta = 0;
+  if (may_spill) {
+    chunks = (n + CH - 1) / CH + (uint64_t)team * fan + 8;
+    data = align_up(chunks * CH * REC_BYTES, 256);
+    meta = align_up(chunks * 4, 256);
+    if (cudaMallocAsync(&stg, 2 * (data + 3 * meta), st) != cudaSuccess) return AGG_ERR_OOM;
+  }
+  for (int a = 0; a < 2; ++a) {
+    uint8_t* area = stg ? static_cast<uint8_t*>(stg) + a * (data + 3 * meta) : nullptr;
+    p.stg[a] = area;
+    p.dir_part[a] = area ? reinterpret_cast<uint32_t*>(area + data) : nullptr;
+    p.dir_count[a] = area ? reinterpret_cast<uint32_t*>(area + data + meta) : nullptr;
+    p.list[a] = area ? reinterpret_cast<uint32_t*>(area + data + 2 * meta) : nullptr;
+    p.max_chunks[a] = area ? chunks : 0;
+  }
+  p.keys = q.d_keys;
+  p.vals = q.d_vals;
+  p.n = n;
+  p.has_vals = q.d_vals != nullptr;
+  p.vec_ok = ((reinterpret_cast<uintptr_t>(q.d_keys) & 15) == 0) &&
+             (!q.d_vals || (reinterpret_cast<uintptr_t>(q.d_vals) & (s->spec.value_type == AGG_I64 ? 15 : 7)) == 0);
+  p.o_keys = q.out.keys;
+  p.o_count = (s->spec.ops & AGG_COUNT) ? q.out.count : nullptr;
+  p.o_sum = (s->spec.ops & AGG_SUM) ? q.out.sum : nullptr;
+  p.o_min = (s->spec.ops & AGG_MIN) ? q.out.min : nullptr;
+  p.o_max = (s->spec.ops & AGG_MAX) ? q.out.max : nullptr;
+  p.o_cap = q.out.capacity;
+  p.o_ngroups = nullptr;
+  p.ctrl = ctrl;
+  p.ent = ent;
+  p.tags = tags;
+  p.slots = (uint32_t)slots;
+  p.seed = s->spec.seed;
+  p.ops = s->spec.ops;
+  p.fan_log2 = log2u(fan);
+  p.lf = s->tune.max_load_factor;
+  p.s_act0 = active_slots(q.expected_groups ? q.expected_groups : (n ? n : 1), p.lf, slots);
+  p.ns = s->tune.smem_entries;
+  p.cache = 1;
+  p.dedup = 1;
+  p.timeout_ns = TIMEOUT_NS;
+  KernelInfo ki = s->ki;
+  ki.blocks = (int)team;
+  if (hash_launch(s->ent_kind, s->spec.value_type, p, ki, st) != cudaSuccess) return AGG_ERR_CUDA;
+  if (stg && cudaFreeAsync(stg, st) != cudaSuccess) return AGG_ERR_CUDA;
+  if (cudaMemcpyAsync(s->pinned + 2 * slot, &ctrl->status_bits, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(s->pinned + 2 * slot + 1, &ctrl->last_n_groups, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaEventRecord(s->events[slot], st) != cudaSuccess)
+    return AGG_ERR_CUDA;
+  sq.info.team_blocks = team;
+  return AGG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+agg_status agg_server_create(const agg_spec* spec, size_t pool_bytes, uint32_t max_active, agg_server** out) {
+  if (!out || !valid_spec(spec) || spec->path != AGG_PATH_HASH || max_active == 0 || max_active > 4096 ||
+      pool_bytes < AGG_MIN_BUDGET)
+    return AGG_ERR_INVALID_ARG;
+  *out = nullptr;
+  agg_server* s = new (std::nothrow) agg_server();
+  if (!s) return AGG_ERR_OOM;
+  auto fail = [&](agg_status st) {
+    agg_server_destroy(s);
+    return st;
+  };
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return AGG_ERR_CUDA;
+  }
+  s->spec = *spec;
+  s->ent_kind = pick_ent(spec);
+  s->es = entry_bytes(s->ent_kind);
+  s->tune = effective(nullptr);
+  if (hash_kernel_info(s->ent_kind, spec->value_type, s->tune.smem_entries, s->device, &s->ki) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AGG_ERR_CUDA);
+  }
+  if (cudaMalloc(reinterpret_cast<void**>(&s->pool), pool_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AGG_ERR_OOM);
+  }
+  s->pool_bytes = pool_bytes;
+  s->free_list[0] = pool_bytes;
+  if (cudaMallocHost(reinterpret_cast<void**>(&s->pinned), 16ull * max_active) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AGG_ERR_OOM);
+  }
+  // keep memory freed by cudaFreeAsync cached in the pool for the next query
+  cudaMemPool_t mp;
+  if (cudaDeviceGetDefaultMemPool(&mp, s->device) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  s->streams.resize(max_active, nullptr);
+  s->events.resize(max_active, nullptr);
+  s->slot_ticket.assign(max_active, -1);
+  for (uint32_t i = 0; i < max_active; ++i)
+    if (cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->events[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AGG_ERR_CUDA);
+    }
+  *out = s;
+  return AGG_OK;
+}
+
+agg_status agg_server_submit(agg_server* s, const agg_query* q, uint64_t* ticket) {
+  if (!s || !q || !ticket) return AGG_ERR_INVALID_ARG;
+  Layout L;
+  if (!layout_for(q->budget, s->es, &L)) return AGG_ERR_BUDGET_TOO_SMALL;
+  if (L.total > s->pool_bytes) return AGG_ERR_INVALID_ARG;  // could never be admitted
+  if (!q->out.keys || (q->n > 0 && !q->d_keys)) return AGG_ERR_INVALID_ARG;
+  const uint64_t t = s->next_ticket++;
+  ServerQuery& sq = s->queries[t];
+  sq.q = *q;
+  sq.info.state = AGG_QUERY_QUEUED;
+  sq.info.t_submit = s->now();
+  s->waiting.push_back(t);
+  s->submitted += 1;
+  *ticket = t;
+  return AGG_OK;
+}
+
+agg_status agg_server_progress(agg_server* s, uint32_t* completed) {
+  if (!s) return AGG_ERR_INVALID_ARG;
+  DeviceGuard g(s->device);
+  uint32_t done = 0;
+  for (size_t slot = 0; slot < s->slot_ticket.size(); ++slot) {
+    if (s->slot_ticket[slot] < 0) continue;
+    const cudaError_t e = cudaEventQuery(s->events[slot]);
+    if (e == cudaErrorNotReady) continue;
+    ServerQuery& sq = s->queries[(uint64_t)s->slot_ticket[slot]];
+    sq.info.t_done = s->now();
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      sq.info.state = AGG_QUERY_FAILED;
+      sq.info.status = AGG_ERR_CUDA;
+    } else {
+      const unsigned long long bits = s->pinned[2 * slot];
+      sq.info.status = status_from_bits(bits);
+      sq.info.state = sq.info.status == AGG_OK ? AGG_QUERY_DONE : AGG_QUERY_FAILED;
+      sq.info.n_groups = s->pinned[2 * slot + 1];
+    }
+    pool_free(s, sq.pool_off, sq.pool_len);
+    s->slot_ticket[slot] = -1;
+    s->running -= 1;
+    s->completed += 1;
+    ++done;
+  }
+  // admission in arrival order: a free slot and room for the declared budget
+  while (!s->waiting.empty()) {
+    int slot = -1;
+    for (size_t i = 0; i < s->slot_ticket.size(); ++i)
+      if (s->slot_ticket[i] < 0) {
+        slot = (int)i;
+        break;
+      }
+    if (slot < 0) break;
+    const uint64_t t = s->waiting.front();
+    ServerQuery& sq = s->queries[t];
+    Layout L;
+    layout_for(sq.q.budget, s->es, &L);
+    uint64_t off = 0;
+    if (!pool_alloc(s, L.total, &off)) break;
+    s->waiting.pop_front();
+    sq.pool_off = off;
+    sq.pool_len = L.total;
+    sq.slot = slot;
+    const agg_status st = server_launch(s, sq, slot);
+    sq.info.t_start = s->now();
+    if (st != AGG_OK) {
+      cudaGetLastError();
+      pool_free(s, off, L.total);
+      sq.info.state = AGG_QUERY_FAILED;
+      sq.info.status = st;
+      sq.info.t_done = sq.info.t_start;
+      s->completed += 1;
+      continue;
+    }
+    sq.info.state = AGG_QUERY_RUNNING;
+    s->slot_ticket[slot] = (int64_t)t;
+    s->running += 1;
+    s->max_conc = std::max<uint64_t>(s->max_conc, s->running);
+  }
+  if (completed) *completed = done;
+  return AGG_OK;
+}
+
+agg_status agg_server_poll(agg_server* s, uint64_t ticket, agg_query_info* info) {
+  if (!s || !info) return AGG_ERR_INVALID_ARG;
+  auto it = s->queries.find(ticket);
+  if (it == s->queries.end()) return AGG_ERR_INVALID_ARG;
+  *info = it->second.info;
+  return AGG_OK;
+}
+
+agg_status agg_server_get_stats(agg_server* s, agg_server_stats* st) {
+  if (!s || !st) return AGG_ERR_INVALID_ARG;
+  st->submitted = s->submitted;
+  st->completed = s->completed;
+  st->running = s->running;
+  st->queued = s->waiting.size();
+  st->pool_bytes = s->pool_bytes;
+  st->pool_in_use = s->in_use;
+  st->pool_peak = s->peak;
+  st->max_concurrent = s->max_conc;
+  return AGG_OK;
+}
+
+agg_status agg_server_destroy(agg_server* s) {
+  if (!s) return AGG_OK;
+  DeviceGuard g(s->device);
+  for (cudaStream_t st : s->streams)
+    if (st) cudaStreamSynchronize(st);
+  cudaGetLastError();
+  for (cudaEvent_t e : s->events)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t st : s->streams)
+    if (st) cudaStreamDestroy(st);
+  if (s->pool) cudaFree(s->pool);
+  if (s->pinned) cudaFreeHost(s->pinned);
+  delete s;
   return AGG_OK;
 }
 

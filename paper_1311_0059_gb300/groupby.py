@@ -9,8 +9,8 @@ import torch
 
 from . import _abi
 from ._abi import (AGG_COUNT, AGG_I32, AGG_I64, AGG_MAX, AGG_MIN, AGG_PATH_HASH, AGG_PATH_SORT, AGG_SUM,
-                   agg_batch_item, agg_batch_tuning, agg_output, agg_plan_info, agg_spec, agg_stats, agg_tuning,
-                   check)
+                   agg_batch_item, agg_batch_tuning, agg_output, agg_plan_info, agg_query, agg_query_info,
+                   agg_server_stats, agg_spec, agg_stats, agg_tuning, check)
 
 ALL_OPS = AGG_COUNT | AGG_SUM | AGG_MIN | AGG_MAX
 
@@ -194,6 +194,61 @@ class Batch:
         if getattr(self, "h", None):
             self.lib.agg_batch_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Queries that arrive over time, admitted against a device memory pool by
+    their declared budgets and run concurrently (agg_server_*)."""
+
+    def __init__(self, pool_bytes: int, max_active: int = 64, ops: int = ALL_OPS, value_type: int = AGG_I64,
+                 seed: int = 0):
+        self.lib = _abi.load()
+        self.spec = make_spec(ops, value_type, AGG_PATH_HASH, 0, seed)
+        self.ops = ops
+        h = ctypes.c_void_p()
+        check(self.lib.agg_server_create(ctypes.byref(self.spec), pool_bytes, max_active, ctypes.byref(h)),
+              "agg_server_create")
+        self.h = h
+        self.keep = {}  # tensors that must live until their query completes
+
+    def submit(self, keys, vals, budget: int, out: Output, expected_groups: int = 0, ready_event=None) -> int:
+        q = agg_query(d_keys=keys.data_ptr(), d_vals=vals.data_ptr() if vals is not None else None, n=keys.numel(),
+                      budget=budget, expected_groups=expected_groups, out=out.abi,
+                      ready=ready_event.cuda_event if ready_event is not None else None)
+        t = ctypes.c_uint64()
+        check(self.lib.agg_server_submit(self.h, ctypes.byref(q), ctypes.byref(t)), "agg_server_submit")
+        self.keep[t.value] = (keys, vals, out, ready_event)
+        return t.value
+
+    def progress(self) -> int:
+        c = ctypes.c_uint32()
+        check(self.lib.agg_server_progress(self.h, ctypes.byref(c)), "agg_server_progress")
+        return c.value
+
+    def poll(self, ticket: int) -> agg_query_info:
+        info = agg_query_info()
+        check(self.lib.agg_server_poll(self.h, ticket, ctypes.byref(info)), "agg_server_poll")
+        return info
+
+    def release(self, ticket: int):
+        self.keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        st = agg_server_stats()
+        check(self.lib.agg_server_get_stats(self.h, ctypes.byref(st)), "agg_server_get_stats")
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.agg_server_destroy(self.h)
+            self.h = None
+            self.keep.clear()
 
     def __del__(self):
         try:

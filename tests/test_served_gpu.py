@@ -1,0 +1,91 @@
+"""The served form: queries arriving over time, admitted against a device
+memory pool by their declared budgets, running concurrently.  Each query's
+result must be the same in the mix as alone (and as the oracle's), exactly;
+admission must never let the admitted budgets exceed the pool."""
+import time
+
+import numpy as np
+import pytest
+
+import datagen as dg
+from _gpu import assert_parity, canon, oracle_expected, to_dev
+
+pytestmark = pytest.mark.gpu
+MB = 1 << 20
+
+
+def test_served_results_equal_alone_and_pool_respected(oracle):
+    import torch
+    from paper_1311_0059_gb300 import _abi
+    from paper_1311_0059_gb300.groupby import GroupBy, Output, Server
+    qs = dg.served_workloads(duration=0.25, rate=160.0, seed=7, rows=(10_000, 400_000), card=(0.001, 0.5),
+                             budget=(MB, 6 * MB))
+    assert len(qs) >= 20
+    pool = 16 * MB
+    srv = Server(pool, max_active=8)
+    data, tickets = [], []
+    t0 = time.perf_counter()
+    for arrival, w in qs:
+        while time.perf_counter() - t0 < arrival:
+            srv.progress()
+        k, v = w.host()
+        dk, dv = to_dev(k), to_dev(v)
+        out = Output(w.n, 15, "cuda")
+        tickets.append(srv.submit(dk, dv, w.budget, out))
+        data.append((k, v, w.budget, out))
+        srv.progress()
+    deadline = time.perf_counter() + 60
+    while srv.stats()["completed"] < len(qs) and time.perf_counter() < deadline:
+        srv.progress()
+    st = srv.stats()
+    assert st["completed"] == len(qs)
+    assert st["pool_peak"] <= pool
+    assert st["max_concurrent"] >= 2, "queries should overlap on the device"
+    for (k, v, b, out), t in zip(data, tickets):
+        info = srv.poll(t)
+        assert info.state == _abi.AGG_QUERY_DONE and info.status == 0
+        assert info.t_done >= info.t_start >= info.t_submit
+        got = canon({f: x.cpu().numpy() for f, x in out.result(info.n_groups).items()})
+        exp = oracle_expected(oracle, k, v)
+        assert_parity(got, exp, what=f"ticket {t} in the mix")
+    # the same queries alone, one at a time
+    for (k, v, b, out), t in list(zip(data, tickets))[:8]:
+        with GroupBy(b) as g:
+            alone = canon({f: x.cpu().numpy() for f, x in g.run(to_dev(k), to_dev(v)).items()})
+        got = canon({f: x.cpu().numpy() for f, x in out.result(srv.poll(t).n_groups).items()})
+        assert_parity(got, alone, what=f"ticket {t}: alone vs in the mix")
+    srv.close()
+
+
+def test_served_admission_waits_for_memory():
+    # three queries whose budgets each take most of the pool: they must run one by one
+    from paper_1311_0059_gb300 import _abi
+    from paper_1311_0059_gb300.groupby import Output, Server
+    pool = 8 * MB
+    srv = Server(pool, max_active=4)
+    ws = [dg.Workload(f"q{i}", n=200_000, domain=50_000, seed=i, budget=6 * MB) for i in range(3)]
+    outs, ts = [], []
+    for w in ws:
+        k, v = w.host()
+        o = Output(w.n, 15, "cuda")
+        ts.append(srv.submit(to_dev(k), to_dev(v), w.budget, o))
+        outs.append(o)
+    srv.progress()
+    st = srv.stats()
+    assert st["running"] == 1 and st["queued"] == 2
+    while srv.stats()["completed"] < 3:
+        srv.progress()
+    assert srv.stats()["max_concurrent"] == 1 and srv.stats()["pool_peak"] <= pool
+    assert all(srv.poll(t).state == _abi.AGG_QUERY_DONE for t in ts)
+    srv.close()
+
+
+def test_served_rejects_budget_larger_than_pool():
+    import torch
+    from paper_1311_0059_gb300 import _abi
+    from paper_1311_0059_gb300.groupby import Output, Server
+    srv = Server(4 * MB, max_active=2)
+    k = torch.zeros(10, dtype=torch.int64, device="cuda")
+    with pytest.raises(_abi.AggError):
+        srv.submit(k, k, 64 * MB, Output(10, 15, "cuda"))
+    srv.close()
