@@ -123,9 +123,10 @@ typedef struct agg_stats {
   uint64_t fan_out;
   uint64_t status_bits;                          /* 1 << agg_status of device-side errors seen */
   uint64_t kernel_launches;                      /* kernels this handle has launched, cumulative */
-  uint64_t phase_ns[8];                          /* hash path, block 0's time per phase: level-0 pass,
+  uint64_t phase_ns[12];                         /* hash path, block 0's time per phase: level-0 pass,
                                                     barrier wait, level-0 emit, partition lists, round
-                                                    aggregation, barrier waits, round emit, total */
+                                                    aggregation, barrier waits, round emit, total,
+                                                    shared-memory rounds: count, scatter, aggregate */
 } agg_stats;
 
 /* Planner output (host-only arithmetic, no GPU needed). */

@@ -56,7 +56,7 @@ class agg_stats(ctypes.Structure):
                 ("spill_bytes_written", _U64), ("spill_bytes_read", _U64), ("rows_at_full", _U64),
                 ("table_slots", _U64), ("table_capacity", _U64), ("table_bytes", _U64), ("budget_bytes", _U64),
                 ("staging_bytes", _U64), ("fan_out", _U64), ("status_bits", _U64), ("kernel_launches", _U64),
-                ("phase_ns", _U64 * 8)]
+                ("phase_ns", _U64 * 12)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

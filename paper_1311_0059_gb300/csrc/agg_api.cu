@@ -534,7 +534,7 @@ agg_status agg_get_stats(agg_handle* h, agg_stats* s) {
   s->spill_bytes_written = spilled * REC_BYTES;
   s->spill_bytes_read = spilled * REC_BYTES;
   s->rows_at_full = c.last_rows_at_full == ~0ull ? 0 : c.last_rows_at_full;
-  for (int i = 0; i < 8; ++i) s->phase_ns[i] = c.last_phase_ns[i];
+  for (int i = 0; i < PHASES; ++i) s->phase_ns[i] = c.last_phase_ns[i];
   s->table_slots = h->slots;
   s->table_capacity = (uint64_t)(h->tune.max_load_factor * (double)h->slots);
   s->table_bytes = h->working_bytes;
@@ -998,8 +998,10 @@ void pool_free(agg_server* s, uint64_t off, uint64_t len) {
 }
 
 // Thread blocks of a query's team: more rows, more blocks (power of two, at
-// most half the GPU so that other queries keep running beside it).
-uint32_t team_for(uint64_t n, uint32_t all_blocks) {
+// most half the GPU so that other queries keep running beside it).  A server
+// that runs one query at a time gives each query the whole GPU.
+uint32_t team_for(uint64_t n, uint32_t all_blocks, uint32_t max_active) {
+  if (max_active == 1) return all_blocks;
   uint32_t b = 8;
   while (b < all_blocks / 2 && (uint64_t)b * (1ull << 18) < n) b <<= 1;
   return std::min(b, std::max(1u, all_blocks / 2));
@@ -1022,7 +1024,7 @@ agg_status server_launch(agg_server* s, ServerQuery& sq, int slot) {
   agg_spec si = s->spec;
   si.expected_groups = q.expected_groups;
   const uint32_t fan = plan_fan(&si, s->tune, n, q.budget, s->es);
-  const uint32_t team = team_for(n, (uint32_t)s->ki.blocks);
+  const uint32_t team = team_for(n, (uint32_t)s->ki.blocks, (uint32_t)s->slot_ticket.size());
   if (q.ready && cudaStreamWaitEvent(st, static_cast<cudaEvent_t>(q.ready), 0) != cudaSuccess) return AGG_ERR_CUDA;
   if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st) != cudaSuccess ||
       hash_init_table(ent, tags, (uint32_t)slots, s->ent_kind, st) != cudaSuccess)

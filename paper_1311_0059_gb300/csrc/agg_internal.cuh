@@ -20,7 +20,7 @@ constexpr uint32_t MIN_SLOTS = 4096;       // smallest active table of a round
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr int64_t EMPTY_KEY = INT64_MIN;   // empty key slot; this one key value lives in a side slot
 constexpr int64_t SKEY_EMPTY = INT64_MIN;  // empty marker of the shared-memory cache
-constexpr int PHASES = 8;                  // phase timers kept by block 0
+constexpr int PHASES = 12;                 // phase timers kept by block 0
 constexpr uint32_t NSUB_MAX = 4096;        // sub-partitions of one shared-memory round
 constexpr uint64_t ROUND_CAP_MAX = 4ull << 20;  // records of one shared-memory round (L2-sized)
 constexpr uint64_t REC_BYTES = 16;         // spilled record: (int64 key, int64 value)

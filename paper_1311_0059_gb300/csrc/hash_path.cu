@@ -191,6 +191,10 @@ __device__ bool grid_barrier(const Team& T, Ctrl* c, uint64_t timeout_ns, Smem& 
   return S.ok != 0;
 }
 
+// Phase indices of Ctrl::phase_ns (block 0's view).
+enum Phase { PH_L0 = 0, PH_L0_WAIT, PH_L0_EMIT, PH_LISTS, PH_ROUND_AGG, PH_ROUND_WAIT, PH_ROUND_EMIT, PH_TOTAL,
+             PH_SUB_COUNT, PH_SUB_SCATTER, PH_SUB_AGG };
+
 // Phase timer of block 0 (diagnostics, reported by agg_get_stats).
 struct Timer {
   uint64_t t;
@@ -277,7 +281,11 @@ __device__ __forceinline__ uint32_t home_bucket(uint64_t h, uint32_t s_act) {
   return (uint32_t)(((h >> 32) * (uint64_t)(s_act / BUCKET)) >> 32);
 }
 
-__device__ __forceinline__ uint32_t key_tag(uint64_t h) { return 0x80u | (uint32_t)(h & 0x7Fu); }
+// Tag byte of a key: 8 hash bits, 1..255 (0 marks a free slot).
+__device__ __forceinline__ uint32_t key_tag(uint64_t h) {
+  const uint32_t t = (uint32_t)(h & 0xFFu);
+  return t ? t : 1u;
+}
 
 // Finds or claims the slot of `key` in its bucket, given the bucket's candidate
 // mask.  A key may live only in its bucket, in the first slot that was free
@@ -703,7 +711,7 @@ __device__ void emit_table(const HashParams& P, const Team& T, uint32_t s_act, u
       for (uint32_t q = 0; q < WPT; ++q) tw[q] = (w0 + q < words) ? __ldcg(P.tags + w0 + q) : 0u;
     }
 #pragma unroll
-    for (uint32_t q = 0; q < WPT; ++q) oc += __popc(tw[q] & 0x80808080u);
+    for (uint32_t q = 0; q < WPT; ++q) oc += __popc(~__vcmpeq4(tw[q], 0u) & 0x01010101u);
     uint32_t total;
     const uint32_t off = block_exclusive_scan(oc, total, S);
     if (threadIdx.x == 0) {
@@ -717,7 +725,7 @@ __device__ void emit_table(const HashParams& P, const Team& T, uint32_t s_act, u
       if (tw[q] == 0) continue;
 #pragma unroll
       for (uint32_t j = 0; j < 4; ++j) {
-        if (((tw[q] >> (8 * j)) & 0x80u) == 0) continue;
+        if (((tw[q] >> (8 * j)) & 0xFFu) == 0) continue;
         emit_one<ENT>(P, Ent<ENT>::at(P.ent, (w0 + q) * 4 + j), pos);
         ++pos;
       }
@@ -830,7 +838,7 @@ __device__ uint32_t sub_emit(const HashParams& P, const Cache& cc, Smem& S, uint
 }
 
 // Sub-partition of a record within its round (hash bits 16..31, independent of
-// the bucket bits 32..63, the tag bits 0..6 and the partition bits 8..15).
+// the bucket bits 32..63, the tag bits 0..7 and the partition bits 8..15).
 __device__ __forceinline__ uint32_t sub_of(uint64_t h, uint32_t nsub) {
   return (uint32_t)((((h >> 16) & 0xFFFFull) * nsub) >> 16);
 }
@@ -856,8 +864,8 @@ __device__ __forceinline__ bool load_chunk_record(const HashParams& P, uint32_t 
 // the level's global table G (or spill further).  Two grid barriers per round;
 // pass C needs none before the next round's pass A.
 template <int ENT>
-__device__ bool smem_round(const HashParams& P, const Team& T, const Level& G, Smem& S, const Cache& cc, uint32_t src,
-                           uint32_t c0,
+__device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const Level& G, Smem& S, const Cache& cc,
+                           uint32_t src, uint32_t c0,
                            uint32_t c1, uint64_t tot, uint32_t par, longlong2* scratch) {
   Ctrl* C = P.ctrl;
   const uint32_t* dcount = P.dir_count[src];
@@ -893,6 +901,7 @@ __device__ bool smem_round(const HashParams& P, const Team& T, const Level& G, S
   for (uint32_t i = threadIdx.x; i < nsub; i += THREADS)
     if (hist[i]) atomicAdd(&C->sub_tot[par][i], hist[i]);
   if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+  tm.lap(T, C, PH_SUB_COUNT);
 
   // ---- pass B: offsets, then scatter into scratch grouped by sub-partition
   {
@@ -957,6 +966,7 @@ __device__ bool smem_round(const HashParams& P, const Team& T, const Level& G, S
     __syncthreads();
   }
   if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+  tm.lap(T, C, PH_SUB_SCATTER);
 
   // ---- pass C: whole sub-partitions aggregated in shared memory
   cache_reset_all(cc, S, Ent<ENT>::MM);
@@ -1004,6 +1014,7 @@ __device__ bool smem_round(const HashParams& P, const Team& T, const Level& G, S
   }
   cache_reset_all(cc, S, Ent<ENT>::MM);
   __syncthreads();
+  tm.lap(T, C, PH_SUB_AGG);
   return true;
 }
 
@@ -1059,8 +1070,6 @@ __device__ void final_step(const HashParams& P, const Team& T, uint32_t levels) 
   C->done_count = 0;
 }
 
-// Phase indices of Ctrl::phase_ns (block 0's view).
-enum Phase { PH_L0 = 0, PH_L0_WAIT, PH_L0_EMIT, PH_LISTS, PH_ROUND_AGG, PH_ROUND_WAIT, PH_ROUND_EMIT, PH_TOTAL };
 
 // ---------------------------------------------------------------- the kernel
 
@@ -1276,7 +1285,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
           tot += r;
           ++q;
         }
-        if (!smem_round<ENT>(P, T, G, S, cc, src, S.begin[p], S.begin[q], tot, rnd & 1, scratch)) return false;
+        if (!smem_round<ENT>(P, T, tm, G, S, cc, src, S.begin[p], S.begin[q], tot, rnd & 1, scratch)) return false;
         if (threadIdx.x == 0 && T.bid == 0) C->rounds += 1;
         ++rnd;
         tm.lap(T, C, PH_ROUND_AGG);
