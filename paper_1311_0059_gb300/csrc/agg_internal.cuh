@@ -22,7 +22,7 @@ constexpr int64_t EMPTY_KEY = INT64_MIN;   // empty key slot; this one key value
 constexpr int64_t SKEY_EMPTY = INT64_MIN;  // empty marker of the shared-memory cache
 constexpr int PHASES = 12;                 // phase timers kept by block 0
 constexpr uint32_t NSUB_MAX = 4096;        // sub-partitions of one shared-memory round
-constexpr uint64_t ROUND_CAP_MAX = 4ull << 20;  // records of one shared-memory round (L2-sized)
+constexpr uint64_t ROUND_CAP_MAX = 8ull << 20;  // records of one shared-memory round (128 MiB of scratch)
 constexpr uint64_t REC_BYTES = 16;         // spilled record: (int64 key, int64 value)
 // One tile adds at most TILE rows to a partition, so at most one new chunk is
 // opened per partition per tile.
@@ -48,6 +48,7 @@ struct alignas(128) Ctrl {
   unsigned long long out_count;    // groups written so far
   unsigned long long pool_next[2]; // chunks handed out per staging area
   unsigned long long rows_at_full; // level-0 row index of the first tile that spilled
+  unsigned long long tile_next;    // level-0 tiles claimed so far (dynamic tile assignment)
   unsigned long long rounds;
   unsigned long long phase_ns[PHASES];
   unsigned long long spill_records[AGG_MAX_LEVELS];
@@ -56,9 +57,8 @@ struct alignas(128) Ctrl {
   unsigned int part_chunks[2][MAX_FAN];
   unsigned int part_cursor[2][MAX_FAN];
   // shared-memory rounds of levels >= 1 (two sets by round parity)
-  unsigned int sub_tot[2][NSUB_MAX];
-  unsigned int sub_cur[2][NSUB_MAX];
-  unsigned int sub_base[2][NSUB_MAX + 1];
+  unsigned int sub_tot[2][NSUB_MAX];       // records per sub-partition (column totals of the scan)
+  unsigned int sub_base[2][NSUB_MAX + 1];  // start of each sub-partition in the scratch
   unsigned long long lvl_sub_records[2];  // records aggregated in shared memory (by round parity)
   unsigned long long lvl_sub_groups[2];   // groups they formed (keys-per-record estimate)
   unsigned int overflow_used[2];          // a key of the level (by parity) went to the global table

@@ -34,6 +34,7 @@ namespace {
 
 constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
 constexpr int WARPS = THREADS / 32;
+constexpr uint32_t TLIST = 128;  // tiles of a round pass whose chunk ids are staged at once
 
 __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
   k ^= k >> 33;
@@ -87,6 +88,60 @@ __device__ __forceinline__ uint32_t byte_mask_bits(uint32_t m) {
   return ((m >> 7) & 1u) | ((m >> 14) & 2u) | ((m >> 21) & 4u) | ((m >> 28) & 8u);
 }
 
+// Adds v to a 64-bit word in shared memory, exactly modulo 2^64, with 32-bit
+// atomics: the low word takes the low half of v and reports the carry it
+// produced; the high word takes the high half plus that carry (skipped when
+// zero, the common case for small values).  64-bit shared-memory additions
+// have no native atomic and contend badly on hot words.
+// Shared-memory accesses of the partial-state tables, in the shared state
+// space explicitly (the tables are reached through pointers, and a generic
+// atomic on shared memory is far slower than a shared one).
+__device__ __forceinline__ uint32_t sh_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ long long sh_ld_volatile_s64(const long long* p) {
+  long long v;
+  asm volatile("ld.volatile.shared.s64 %0, [%1];" : "=l"(v) : "r"(sh_addr(p)) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint32_t sh_ld_volatile_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(sh_addr(p)) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ long long sh_cas_s64(long long* p, long long cmp, long long val) {
+  long long old;
+  asm volatile("atom.shared.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "r"(sh_addr(p)), "l"(cmp), "l"(val) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ uint32_t sh_atom_add_u32(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(sh_addr(p)), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void sh_red_add_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(sh_addr(p)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void sh_red_min_s64(long long* p, long long v) {
+  asm volatile("red.shared.min.s64 [%0], %1;" ::"r"(sh_addr(p)), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void sh_red_max_s64(long long* p, long long v) {
+  asm volatile("red.shared.max.s64 [%0], %1;" ::"r"(sh_addr(p)), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void smem_add_u64(unsigned long long* p, unsigned long long v) {
+  uint32_t* w = reinterpret_cast<uint32_t*>(p);
+  const uint32_t lo = (uint32_t)v;
+  const uint32_t old = sh_atom_add_u32(w, lo);
+  const uint32_t inc = (uint32_t)(v >> 32) + ((uint32_t)(old + lo) < old ? 1u : 0u);
+  if (inc) sh_red_add_u32(w + 1, inc);
+}
+
 // ---------------------------------------------------------------- shared memory
 
 struct Smem {
@@ -104,23 +159,30 @@ struct Smem {
   uint32_t cache_used;
   uint32_t first_spill;
   uint32_t tiles;      // tiles processed by this block (adaptive sampling clock)
+  uint32_t flush_tiles;  // tiles since the shared-memory cache was last flushed
   uint32_t use_cache;
   uint32_t use_dedup;
   uint32_t st_rows, st_hits, st_dups;
+  unsigned long long tile_q[2];  // level-0 tiles claimed by this block (current, next) by iteration parity
+  uint32_t tl_chunk[TLIST];     // staged tiles of a round pass: chunk id
+  uint32_t tl_count[TLIST];     // and its record count
 };
 
+// Shared-memory table of partial states.  Counts are 32-bit (an entry is
+// flushed before it can see 2^31 rows); sums are 64-bit words updated with
+// smem_add_u64; MIN/MAX use the native 64-bit atomics.
 struct Cache {
   long long* key;
-  unsigned long long* cnt;
   unsigned long long* sum;
   long long* mn;
   long long* mx;
+  unsigned* cnt;
   uint32_t* slot;
   uint32_t n;  // 0 = disabled
 };
 
 __host__ __device__ inline size_t cache_bytes(uint32_t ns, bool mm) {
-  return (size_t)ns * (8 + 8 + 8 + 4 + (mm ? 16 : 0));
+  return (size_t)ns * (8 + 8 + 4 + 4 + (mm ? 16 : 0));
 }
 
 __device__ inline Cache carve_cache(unsigned char* base, uint32_t ns, bool mm) {
@@ -128,8 +190,6 @@ __device__ inline Cache carve_cache(unsigned char* base, uint32_t ns, bool mm) {
   c.n = ns;
   unsigned char* p = base;
   c.key = reinterpret_cast<long long*>(p);
-  p += (size_t)ns * 8;
-  c.cnt = reinterpret_cast<unsigned long long*>(p);
   p += (size_t)ns * 8;
   c.sum = reinterpret_cast<unsigned long long*>(p);
   p += (size_t)ns * 8;
@@ -141,6 +201,8 @@ __device__ inline Cache carve_cache(unsigned char* base, uint32_t ns, bool mm) {
   } else {
     c.mn = c.mx = nullptr;
   }
+  c.cnt = reinterpret_cast<unsigned*>(p);
+  p += (size_t)ns * 4;
   c.slot = reinterpret_cast<uint32_t*>(p);
   return c;
 }
@@ -288,25 +350,29 @@ __device__ __forceinline__ uint32_t key_tag(uint64_t h) {
 }
 
 // Finds or claims the slot of `key` in its bucket, given the bucket's candidate
-// mask.  A key may live only in its bucket, in the first slot that was free
-// when it arrived: the candidates are visited in slot order; a free slot is
-// claimed by a 64-bit CAS; a slot taken meanwhile by another key is passed.
-// Returns the slot when the key is (now) resident, -1 when the bucket holds 32
-// other keys (the key spills).  *claimed is set when this call inserted it.
+// mask and the key word of its first candidate slot (`k_first`, loaded by the
+// caller so that the loads of several rows overlap).  A key may live only in
+// its bucket, in the first slot that was free when it arrived: the candidates
+// are visited in slot order; a free slot is claimed by a 64-bit CAS; a slot
+// taken meanwhile by another key is passed.  Returns the slot when the key is
+// (now) resident, -1 when the bucket holds 32 other keys (the key spills).
+// *claimed is set when this call inserted it.
 template <int ENT>
 __device__ long long probe_table(const HashParams& P, uint32_t b, uint32_t cand, long long key, uint32_t tag,
-                                 uint32_t& claimed) {
+                                 uint32_t& claimed, long long k_first) {
   if (key == EMPTY_KEY) {  // the empty marker value itself: side slot, always resident
     uint8_t* tb = reinterpret_cast<uint8_t*>(P.tags) + P.slots;
     if (__ldcg(tb) == 0) __stcg(tb, (uint8_t)0x80);
     return P.slots;
   }
+  bool first = true;
   while (cand) {
     const uint32_t i = __ffs(cand) - 1;
     cand &= cand - 1;
     const uint32_t slot = b * BUCKET + i;
     long long* kp = reinterpret_cast<long long*>(Ent<ENT>::at(P.ent, slot));
-    const long long k2 = __ldcg(kp);
+    const long long k2 = first ? k_first : __ldcg(kp);
+    first = false;
     if (k2 == key) return slot;
     if (k2 != EMPTY_KEY) continue;
     const long long old = (long long)atomicCAS(reinterpret_cast<unsigned long long*>(kp),
@@ -339,13 +405,13 @@ __device__ __forceinline__ bool cache_hit(const Cache& cc, long long key, uint64
   uint32_t idx = (uint32_t)(h >> 16) & (cc.n - 1);
 #pragma unroll 1
   for (int i = 0; i < 8; ++i) {
-    const long long kk = *reinterpret_cast<volatile long long*>(cc.key + idx);
+    const long long kk = sh_ld_volatile_s64(cc.key + idx);
     if (kk == key) {
-      atomicAdd(cc.cnt + idx, c);
-      atomicAdd(cc.sum + idx, s);
+      sh_red_add_u32(cc.cnt + idx, (uint32_t)c);
+      smem_add_u64(cc.sum + idx, s);
       if (Ent<ENT>::MM) {
-        atomicMin(cc.mn + idx, mn);
-        atomicMax(cc.mx + idx, mx);
+        sh_red_min_s64(cc.mn + idx, mn);
+        sh_red_max_s64(cc.mx + idx, mx);
       }
       return true;
     }
@@ -357,18 +423,17 @@ __device__ __forceinline__ bool cache_hit(const Cache& cc, long long key, uint64
 
 __device__ __forceinline__ void cache_insert(const Cache& cc, Smem& S, long long key, uint64_t h, uint32_t slot) {
   if (cc.n == 0 || key == SKEY_EMPTY) return;
-  if (*reinterpret_cast<volatile uint32_t*>(&S.cache_used) >= cc.n / 2) return;
+  if (sh_ld_volatile_u32(&S.cache_used) >= cc.n / 2) return;
   uint32_t idx = (uint32_t)(h >> 16) & (cc.n - 1);
 #pragma unroll 1
   for (int i = 0; i < 8; ++i) {
-    const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(cc.key + idx),
-                                             (unsigned long long)SKEY_EMPTY, (unsigned long long)key);
-    if (old == (unsigned long long)SKEY_EMPTY) {
+    const long long old = sh_cas_s64(cc.key + idx, SKEY_EMPTY, key);
+    if (old == SKEY_EMPTY) {
       cc.slot[idx] = slot;
-      atomicAdd(&S.cache_used, 1u);
+      sh_red_add_u32(&S.cache_used, 1u);
       return;
     }
-    if ((long long)old == key) return;
+    if (old == key) return;
     idx = (idx + 1) & (cc.n - 1);
   }
 }
@@ -392,9 +457,16 @@ __device__ void cache_flush(const HashParams& P, const Cache& cc, Smem& S) {
       cc.mx[i] = INT64_MIN;
     }
   }
-  if (threadIdx.x == 0) S.cache_used = 0;
+  if (threadIdx.x == 0) {
+    S.cache_used = 0;
+    S.flush_tiles = 0;
+  }
   __syncthreads();
 }
+
+// A cache entry counts in 32 bits: flushing at least every 2^20 tiles (2^31
+// rows of one block) keeps every count below 2^32.
+constexpr uint32_t CACHE_FLUSH_TILES = 1u << 20;
 
 // ---------------------------------------------------------------- one tile of rows
 
@@ -423,12 +495,14 @@ __device__ __forceinline__ void adapt_end_tile(Smem& S, bool cache_allowed, bool
       S.st_rows = S.st_hits = S.st_dups = 0;
     }
     S.tiles += 1;
+    S.flush_tiles += 1;
   }
 }
 
 template <int ENT>
 __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, const Cache& cc, long long (&k)[RPT],
-                                 long long (&v)[RPT], const bool (&need)[RPT], uint64_t tile_row0, bool cache_ins);
+                                 long long (&v)[RPT], const uint64_t (&h)[RPT], const bool (&need)[RPT],
+                                 uint64_t tile_row0, bool cache_ins);
 
 // Aggregates up to RPT rows per thread (block-uniform call), then spills the
 // rows whose keys are not resident.  `tile_row0` orders level-0 tiles.
@@ -440,16 +514,19 @@ __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const
   const bool use_dedup = S.use_dedup;
   const bool sampling = (S.tiles % SAMPLE_PERIOD) < SAMPLE_TILES;
   bool need[RPT];
+  uint64_t h[RPT];  // each row's hash under this level's seed, computed once
   uint32_t hits = 0, dups = 0;
 
   // ---- shared-memory cache of resident groups (with warp dedup of equal keys)
 #pragma unroll
-  for (int r = 0; r < RPT; ++r) need[r] = valid[r];
+  for (int r = 0; r < RPT; ++r) {
+    need[r] = valid[r];
+    h[r] = fmix64((uint64_t)k[r] ^ L.seed);
+  }
   if (use_cache) {
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       const bool val = valid[r];
-      const uint64_t h = fmix64((uint64_t)k[r] ^ L.seed);
       uint32_t peers = 1u << lane, leader = lane;
       unsigned long long gc = 1, gs = (unsigned long long)v[r];
       long long gmn = v[r], gmx = v[r];
@@ -477,7 +554,7 @@ __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const
       }
       bool hit = false;
       if (val && lane == leader) {
-        hit = cache_hit<ENT>(cc, k[r], h, gc, gs, gmn, gmx);
+        hit = cache_hit<ENT>(cc, k[r], h[r], gc, gs, gmn, gmx);
         hits += hit ? (uint32_t)gc : 0u;
       }
       if (use_dedup) hit = __shfl_sync(FULL_MASK, hit, leader);
@@ -508,7 +585,7 @@ __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const
     }
   }
 
-  global_and_spill<ENT>(P, L, S, cc, k, v, need, tile_row0, use_cache || sampling);
+  global_and_spill<ENT>(P, L, S, cc, k, v, h, need, tile_row0, use_cache || sampling);
 }
 
 // Updates the global table for every row with need[r] set (claiming slots for
@@ -517,16 +594,24 @@ __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const
 // slots in the shared-memory cache.
 template <int ENT>
 __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, const Cache& cc, long long (&k)[RPT],
-                                 long long (&v)[RPT], const bool (&need)[RPT], uint64_t tile_row0, bool cache_ins) {
+                                 long long (&v)[RPT], const uint64_t (&h)[RPT], const bool (&need)[RPT],
+                                 uint64_t tile_row0, bool cache_ins) {
   const uint32_t lane = threadIdx.x & 31;
   // ---- global table: bucket tags of every remaining row first, then resolve
   uint32_t cand[RPT];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     cand[r] = 0;
-    if (need[r] && k[r] != EMPTY_KEY) {
-      const uint64_t h = fmix64((uint64_t)k[r] ^ L.seed);
-      cand[r] = bucket_candidates(P, home_bucket(h, L.s_act), key_tag(h) * 0x01010101u);
+    if (need[r] && k[r] != EMPTY_KEY) cand[r] = bucket_candidates(P, home_bucket(h[r], L.s_act), key_tag(h[r]) * 0x01010101u);
+  }
+  // key word of every row's first candidate slot, all loads in flight together
+  long long kf[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    kf[r] = EMPTY_KEY;
+    if (cand[r]) {
+      const uint32_t slot = home_bucket(h[r], L.s_act) * BUCKET + (__ffs(cand[r]) - 1);
+      kf[r] = __ldcg(reinterpret_cast<const long long*>(Ent<ENT>::at(P.ent, slot)));
     }
   }
   bool sp[RPT];
@@ -535,12 +620,12 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
   for (int r = 0; r < RPT; ++r) {
     sp[r] = false;
     if (!need[r]) continue;
-    const uint64_t h = fmix64((uint64_t)k[r] ^ L.seed);
     uint32_t claimed = 0;
-    const long long slot = probe_table<ENT>(P, home_bucket(h, L.s_act), cand[r], k[r], key_tag(h), claimed);
+    const long long slot =
+        probe_table<ENT>(P, home_bucket(h[r], L.s_act), cand[r], k[r], key_tag(h[r]), claimed, kf[r]);
     if (slot >= 0) {
       Ent<ENT>::add(Ent<ENT>::at(P.ent, (uint32_t)slot), P.ops, 1ull, (unsigned long long)v[r], v[r], v[r]);
-      if (cache_ins) cache_insert(cc, S, k[r], h, (uint32_t)slot);
+      if (cache_ins) cache_insert(cc, S, k[r], h[r], (uint32_t)slot);
     } else {
       sp[r] = true;
       any_sp = true;
@@ -557,14 +642,14 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
   uint32_t part[RPT], rank[RPT];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    part[r] = (uint32_t)(fmix64((uint64_t)k[r] ^ L.seed) >> 8) & L.fan_mask;
+    part[r] = (uint32_t)(h[r] >> 8) & L.fan_mask;
     const uint32_t vm = __ballot_sync(FULL_MASK, sp[r]);
     rank[r] = 0;
     if (sp[r]) {
       const uint32_t pm = __match_any_sync(vm, part[r]);
       const int ldr = __ffs(pm) - 1;
       uint32_t base = 0;
-      if ((int)lane == ldr) base = atomicAdd(&S.cnt[part[r]], (uint32_t)__popc(pm));
+      if ((int)lane == ldr) base = sh_atom_add_u32(&S.cnt[part[r]], (uint32_t)__popc(pm));
       base = __shfl_sync(pm, base, ldr);
       rank[r] = base + __popc(pm & lanemask_lt());
     }
@@ -621,7 +706,7 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
       S.fill[p] = f + c;
     }
     S.cnt[p] = 0;
-    atomicAdd(&S.spilled, (unsigned long long)c);
+    smem_add_u64(&S.spilled, (unsigned long long)c);
   }
   __syncthreads();
 }
@@ -760,18 +845,17 @@ __device__ __forceinline__ bool sub_upsert(const Cache& cc, long long key, uint6
   uint32_t idx = (uint32_t)(h >> 32) & (cc.n - 1);
 #pragma unroll 1
   for (int i = 0; i < 16; ++i) {
-    long long kk = *reinterpret_cast<volatile long long*>(cc.key + idx);
+    long long kk = sh_ld_volatile_s64(cc.key + idx);
     if (kk == SKEY_EMPTY) {
-      kk = (long long)atomicCAS(reinterpret_cast<unsigned long long*>(cc.key + idx), (unsigned long long)SKEY_EMPTY,
-                                (unsigned long long)key);
+      kk = sh_cas_s64(cc.key + idx, SKEY_EMPTY, key);
       if (kk == SKEY_EMPTY) kk = key;
     }
     if (kk == key) {
-      atomicAdd(cc.cnt + idx, 1ull);
-      atomicAdd(cc.sum + idx, (unsigned long long)v);
+      sh_red_add_u32(cc.cnt + idx, 1u);
+      smem_add_u64(cc.sum + idx, (unsigned long long)v);
       if (Ent<ENT>::MM) {
-        atomicMin(cc.mn + idx, v);
-        atomicMax(cc.mx + idx, v);
+        sh_red_min_s64(cc.mn + idx, v);
+        sh_red_max_s64(cc.mx + idx, v);
       }
       return true;
     }
@@ -856,17 +940,59 @@ __device__ __forceinline__ bool load_chunk_record(const HashParams& P, uint32_t 
   return true;
 }
 
+// Stages the chunk id and record count of this block's tiles tb, tb + nb, ...
+// (TLIST of them) of a round in shared memory, so that the record loads of a
+// tile do not wait on two dependent loads of the chunk directory.  Returns the
+// number of staged tiles.  Block-uniform call.
+__device__ uint32_t stage_tiles(const Team& T, Smem& S, const uint32_t* list, const uint32_t* dcount, uint32_t c0,
+                                uint64_t ntiles, uint64_t tb) {
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < TLIST; j += THREADS) {
+    const uint64_t t = tb + (uint64_t)j * T.nb;
+    uint32_t ch = 0, cnt = 0;
+    if (t < ntiles) {
+      ch = __ldcg(list + c0 + (uint32_t)t);
+      cnt = __ldcg(dcount + ch);
+    }
+    S.tl_chunk[j] = ch;
+    S.tl_count[j] = cnt;
+  }
+  __syncthreads();
+  const uint64_t left = (ntiles - tb + T.nb - 1) / T.nb;
+  return left < TLIST ? (uint32_t)left : TLIST;
+}
+
+// Record `off` of staged tile j (false past the tile's count).
+__device__ __forceinline__ bool staged_record(const HashParams& P, uint32_t src, const Smem& S, uint32_t j,
+                                              uint32_t off, long long& k, long long& v, bool keep_in_l2) {
+  if (off >= S.tl_count[j]) return false;
+  const longlong2* a = reinterpret_cast<const longlong2*>(P.stg[src] + ((size_t)S.tl_chunk[j] * CH + off) * REC_BYTES);
+  const longlong2 rec = keep_in_l2 ? __ldcg(a) : __ldcs(a);
+  k = rec.x;
+  v = rec.y;
+  return true;
+}
+
+__device__ __forceinline__ void prefetch_staged(const HashParams& P, uint32_t src, const Smem& S, uint32_t j) {
+  prefetch_l2(P.stg[src] + (size_t)S.tl_chunk[j] * CH * REC_BYTES, S.tl_count[j] * (uint32_t)REC_BYTES);
+}
+
 // One shared-memory round over the chunks [c0, c1) of the source area holding
-// `tot` records.  Pass A counts records per sub-partition; pass B scatters them
-// into the scratch memory grouped by sub-partition (exact offsets, cursors per
-// sub-partition); pass C lets each block aggregate whole sub-partitions in its
-// shared-memory table and emit them.  Keys that overflow a block's table go to
-// the level's global table G (or spill further).  Two grid barriers per round;
-// pass C needs none before the next round's pass A.
+// `tot` records.  Pass A: every block counts its records per sub-partition and
+// stores its counts as one row of the histogram matrix `hrows` (team blocks ×
+// sub-partitions, row stride `hstride` words).  Scan: the team turns the
+// columns into per-block exclusive offsets in place and stores each column's
+// total.  Pass B: every block scatters its records into the scratch memory
+// grouped by sub-partition, through block-private cursors in shared memory
+// (start of the sub-partition + this block's offset in it), so neither pass
+// needs a global atomic.  Pass C lets each block aggregate whole
+// sub-partitions in its shared-memory table and emit them.  Keys that overflow
+// a block's table go to the level's global table G (or spill further).  Three
+// grid barriers per round; pass C needs none before the next round's pass A.
 template <int ENT>
 __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const Level& G, Smem& S, const Cache& cc,
-                           uint32_t src, uint32_t c0,
-                           uint32_t c1, uint64_t tot, uint32_t par, longlong2* scratch) {
+                           uint32_t src, uint32_t c0, uint32_t c1, uint64_t tot, uint32_t par, longlong2* scratch,
+                           uint32_t* hrows, uint32_t hstride) {
   Ctrl* C = P.ctrl;
   const uint32_t* dcount = P.dir_count[src];
   const uint32_t* list = P.list[src];
@@ -878,32 +1004,71 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
   if (est > 1.0) est = 1.0;
   const double subkeys = 0.55 * (double)cc.n;
   uint64_t nsub = (uint64_t)((double)tot * est / subkeys) + 1;
-  const uint64_t nsub_cap = (2ull * cc.n < NSUB_MAX) ? 2ull * cc.n : NSUB_MAX;
+  const uint64_t nsub_cap = (2ull * cc.n < hstride) ? 2ull * cc.n : hstride;
   if (nsub > nsub_cap) nsub = nsub_cap;
-  uint32_t* hist = reinterpret_cast<uint32_t*>(cc.key);
-  uint32_t* base = reinterpret_cast<uint32_t*>(cc.key);
-  uint32_t* tcnt = reinterpret_cast<uint32_t*>(cc.cnt);
-  uint32_t* toff = reinterpret_cast<uint32_t*>(cc.sum);
-  const uint32_t lane = threadIdx.x & 31;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(cc.key);  // pass A: counts; pass B: sub-partition starts
+  uint32_t* cur = reinterpret_cast<uint32_t*>(cc.sum);   // pass B: this block's write cursors
+  uint32_t* myrow = hrows + (size_t)T.bid * hstride;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  // ---- pass A: records per sub-partition
+  // ---- pass A: records per sub-partition, one histogram row per block
   for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) hist[i] = 0;
-  __syncthreads();
-  for (uint64_t t = T.bid; t < ntiles; t += T.nb) {
+  for (uint64_t tb = T.bid; tb < ntiles; tb += (uint64_t)TLIST * T.nb) {
+    const uint32_t nj = stage_tiles(T, S, list, dcount, c0, ntiles, tb);
+    if (threadIdx.x < 2 && threadIdx.x < nj) prefetch_staged(P, src, S, threadIdx.x);
+    for (uint32_t j = 0; j < nj; j += 2) {  // two tiles per step: 2 * RPT loads in flight per thread
+      if (threadIdx.x < 2 && j + 2 + threadIdx.x < nj) prefetch_staged(P, src, S, j + 2 + threadIdx.x);
+      long long k[2 * RPT];
+      bool ok[2 * RPT];
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      long long k, v;
-      if (load_chunk_record(P, src, list, dcount, c0, t, r, k, v))
-        atomicAdd(&hist[sub_of(fmix64((uint64_t)k ^ G.seed), (uint32_t)nsub)], 1u);
+      for (int r = 0; r < 2 * RPT; ++r) {  // keys only
+        const uint32_t jj = j + (uint32_t)(r / RPT);
+        const uint32_t off = (uint32_t)(r % RPT) * THREADS + threadIdx.x;
+        ok[r] = jj < nj && off < S.tl_count[jj];
+        k[r] = ok[r] ? __ldcs(reinterpret_cast<const long long*>(P.stg[src] +
+                                                                 ((size_t)S.tl_chunk[jj] * CH + off) * REC_BYTES))
+                     : 0;
+      }
+#pragma unroll
+      for (int r = 0; r < 2 * RPT; ++r)
+        if (ok[r]) sh_red_add_u32(&hist[sub_of(fmix64((uint64_t)k[r] ^ G.seed), (uint32_t)nsub)], 1u);
     }
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < nsub; i += THREADS)
-    if (hist[i]) atomicAdd(&C->sub_tot[par][i], hist[i]);
+  for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) __stcg(myrow + i, hist[i]);
+  if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+
+  // ---- scan: a block takes 32 columns at a time; its warps split the team's
+  // rows, sum their share, exchange the sums, then write the exclusive offsets
+  {
+    uint32_t* wsum = reinterpret_cast<uint32_t*>(cc.key);  // WARPS x 32 partial sums
+    const uint32_t rpw = (T.nb + WARPS - 1) / WARPS;
+    const uint32_t b0 = warp * rpw, b1 = b0 + rpw < T.nb ? b0 + rpw : T.nb;
+    for (uint64_t g = T.bid; g * 32 < nsub; g += T.nb) {
+      const uint32_t col = (uint32_t)g * 32 + lane;
+      uint32_t part = 0;
+      if (col < nsub)
+        for (uint32_t b = b0; b < b1; ++b) part += __ldcg(hrows + (size_t)b * hstride + col);
+      wsum[warp * 32 + lane] = part;
+      __syncthreads();
+      uint32_t acc = 0;
+      for (uint32_t w = 0; w < warp; ++w) acc += wsum[w * 32 + lane];
+      if (col < nsub) {
+        if (warp == WARPS - 1) __stcg(&C->sub_tot[par][col], acc + part);
+        for (uint32_t b = b0; b < b1; ++b) {
+          uint32_t* q = hrows + (size_t)b * hstride + col;
+          const uint32_t x = __ldcg(q);
+          __stcg(q, acc);
+          acc += x;
+        }
+      }
+      __syncthreads();
+    }
+  }
   if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
   tm.lap(T, C, PH_SUB_COUNT);
 
-  // ---- pass B: offsets, then scatter into scratch grouped by sub-partition
+  // ---- pass B: sub-partition starts, this block's cursors, then the scatter
   {
     const uint32_t per = (uint32_t)((nsub + THREADS - 1) / THREADS);
     const uint32_t s0 = threadIdx.x * per;
@@ -914,67 +1079,51 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
     uint32_t acc = block_exclusive_scan(mine, total, S);
     for (uint32_t i = 0; i < per; ++i) {
       if (s0 + i >= nsub) break;
-      base[s0 + i] = acc;
+      hist[s0 + i] = acc;
       if (T.bid == 0) C->sub_base[par][s0 + i] = acc;
       acc += __ldcg(&C->sub_tot[par][s0 + i]);
     }
     if (T.bid == 0 && threadIdx.x == 0) C->sub_base[par][nsub] = total;
-    for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) tcnt[i] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) cur[i] = hist[i] + __ldcg(myrow + i);
     __syncthreads();
   }
-  for (uint64_t t = T.bid; t < ntiles; t += T.nb) {
-    if (threadIdx.x == 0 && t + T.nb < ntiles) {
-      const uint32_t nc = __ldcg(list + c0 + (uint32_t)(t + T.nb));
-      prefetch_l2(P.stg[src] + (size_t)nc * CH * REC_BYTES, __ldcg(dcount + nc) * (uint32_t)REC_BYTES);
-    }
+  for (uint64_t tb = T.bid; tb < ntiles; tb += (uint64_t)TLIST * T.nb) {
+   const uint32_t nj = stage_tiles(T, S, list, dcount, c0, ntiles, tb);
+   for (uint32_t j = 0; j < nj; ++j) {
+    if (threadIdx.x == 0 && j + 1 < nj) prefetch_staged(P, src, S, j + 1);
     long long k[RPT], v[RPT];
-    uint32_t sb[RPT], rk[RPT];
+    uint32_t sb[RPT];
     bool ok[RPT];
 #pragma unroll
+    for (int r = 0; r < RPT; ++r)
+      ok[r] = staged_record(P, src, S, j, (uint32_t)r * THREADS + threadIdx.x, k[r], v[r], false);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) sb[r] = ok[r] ? sub_of(fmix64((uint64_t)k[r] ^ G.seed), (uint32_t)nsub) : 0u;
+#pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      ok[r] = load_chunk_record(P, src, list, dcount, c0, t, r, k[r], v[r]);
-      sb[r] = ok[r] ? sub_of(fmix64((uint64_t)k[r] ^ G.seed), (uint32_t)nsub) : 0u;
       const uint32_t vm = __ballot_sync(FULL_MASK, ok[r]);
-      rk[r] = 0;
       if (ok[r]) {
         const uint32_t pm = __match_any_sync(vm, sb[r]);
         const int ldr = __ffs(pm) - 1;
         uint32_t b0 = 0;
-        if ((int)lane == ldr) b0 = atomicAdd(&tcnt[sb[r]], (uint32_t)__popc(pm));
+        if ((int)lane == ldr) b0 = sh_atom_add_u32(&cur[sb[r]], (uint32_t)__popc(pm));
         b0 = __shfl_sync(pm, b0, ldr);
-        rk[r] = b0 + __popc(pm & lanemask_lt());
+        const uint64_t at = (uint64_t)b0 + __popc(pm & lanemask_lt());
+        longlong2 rec;
+        rec.x = k[r];
+        rec.y = v[r];
+        if (at < tot) scratch[at] = rec;
+        else set_status(C, AGG_ERR_INTERNAL);
       }
     }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) {
-      const uint32_t c = tcnt[i];
-      if (c) toff[i] = atomicAdd(&C->sub_cur[par][i], c);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      if (!ok[r]) continue;
-      longlong2 rec;
-      rec.x = k[r];
-      rec.y = v[r];
-      const uint64_t at = (uint64_t)base[sb[r]] + toff[sb[r]] + rk[r];
-      if (at < tot) scratch[at] = rec;
-      else set_status(C, AGG_ERR_INTERNAL);
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) tcnt[i] = 0;
-    __syncthreads();
+   }
   }
   if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
   tm.lap(T, C, PH_SUB_SCATTER);
 
   // ---- pass C: whole sub-partitions aggregated in shared memory
   cache_reset_all(cc, S, Ent<ENT>::MM);
-  if (T.bid == 0)  // counters of this parity are next used two rounds on
-    for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) {
-      C->sub_tot[par][i] = 0;
-      C->sub_cur[par][i] = 0;
-    }
   __syncthreads();
   unsigned long long my_recs = 0, my_groups = 0;
   for (uint32_t sbi = T.bid; sbi < nsub; sbi += T.nb) {
@@ -986,22 +1135,27 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
     bool overflow = false;
     for (uint32_t t0 = lo; t0 < hi; t0 += TILE) {
       long long k[RPT], v[RPT];
-      bool need[RPT];
+      uint64_t h[RPT];
+      bool need[RPT], in[RPT];
 #pragma unroll
-      for (int r = 0; r < RPT; ++r) {
+      for (int r = 0; r < RPT; ++r) {  // all loads first
         const uint32_t i = t0 + (uint32_t)r * THREADS + threadIdx.x;
-        need[r] = false;
+        in[r] = i < hi;
         k[r] = 0;
         v[r] = 0;
-        if (i < hi) {
+        if (in[r]) {
           const longlong2 rec = scratch[i];
           k[r] = rec.x;
           v[r] = rec.y;
-          need[r] = !sub_upsert<ENT>(cc, k[r], fmix64((uint64_t)k[r] ^ G.seed), v[r]);
-          overflow |= need[r];
         }
       }
-      global_and_spill<ENT>(P, G, S, cc, k, v, need, 0, false);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        h[r] = fmix64((uint64_t)k[r] ^ G.seed);
+        need[r] = in[r] && !sub_upsert<ENT>(cc, k[r], h[r], v[r]);
+        overflow |= need[r];
+      }
+      global_and_spill<ENT>(P, G, S, cc, k, v, h, need, 0, false);
     }
     if (overflow) atomicOr(&C->overflow_used[G.level & 1], 1u);
     __syncthreads();
@@ -1059,6 +1213,7 @@ __device__ void final_step(const HashParams& P, const Team& T, uint32_t levels) 
   C->pool_next[0] = 0;
   C->pool_next[1] = 0;
   C->rows_at_full = ~0ull;
+  C->tile_next = 0;
   C->rounds = 0;
   for (int s = 0; s < 2; ++s)
     for (int p = 0; p < MAX_FAN; ++p) {
@@ -1104,6 +1259,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     S.spilled = 0;
     S.first_spill = 1;
     S.tiles = 0;
+    S.flush_tiles = 0;
     S.use_cache = cc.n != 0 && P.cache != 0;
     S.use_dedup = P.dedup;
     S.st_rows = S.st_hits = S.st_dups = 0;
@@ -1118,16 +1274,27 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     L.s_act = P.s_act0;
     L.dst = 0;
     L.fan_mask = fan - 1;
+    // Tiles are claimed dynamically from a per-run counter, one iteration
+    // ahead so that the next tile can be staged in L2 while this one runs.
     const uint64_t ntiles = (P.n + TILE - 1) / TILE;
-    for (uint64_t t = T.bid; t < ntiles; t += T.nb) {
+    if (threadIdx.x == 0) S.tile_q[0] = atomicAdd(&C->tile_next, 1ull);
+    for (uint32_t it = 0;; ++it) {
+      __syncthreads();  // tile_q[it & 1] is visible; every thread is done with the previous tile
+      const uint64_t t = S.tile_q[it & 1];
+      if (t >= ntiles) break;
+      if (S.flush_tiles >= CACHE_FLUSH_TILES) cache_flush<ENT>(P, cc, S);
       const uint64_t row0 = t * TILE;
-      if (threadIdx.x == 0 && P.vec_ok && t + T.nb < ntiles) {  // stage this block's next tile in L2
-        const uint64_t nr0 = (t + T.nb) * TILE;
-        const uint64_t nrows = P.n - nr0 < (uint64_t)TILE ? P.n - nr0 : (uint64_t)TILE;
-        prefetch_l2(P.keys + nr0, (uint32_t)(nrows * 8));
-        if (P.has_vals)
-          prefetch_l2(static_cast<const char*>(P.vals) + nr0 * (VT == AGG_I64 ? 8 : 4),
-                      (uint32_t)(nrows * (VT == AGG_I64 ? 8 : 4)));
+      if (threadIdx.x == 0) {
+        const uint64_t nt = atomicAdd(&C->tile_next, 1ull);
+        S.tile_q[(it + 1) & 1] = nt;
+        if (P.vec_ok && nt < ntiles) {  // stage the next tile in L2
+          const uint64_t nr0 = nt * TILE;
+          const uint64_t nrows = P.n - nr0 < (uint64_t)TILE ? P.n - nr0 : (uint64_t)TILE;
+          prefetch_l2(P.keys + nr0, (uint32_t)(nrows * 8));
+          if (P.has_vals)
+            prefetch_l2(static_cast<const char*>(P.vals) + nr0 * (VT == AGG_I64 ? 8 : 4),
+                        (uint32_t)(nrows * (VT == AGG_I64 ? 8 : 4)));
+        }
       }
       adapt_begin_tile(S, cc.n != 0 && P.cache != 0, P.dedup != 0);
       __syncthreads();
@@ -1220,7 +1387,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
          c += (unsigned long long)T.nb * THREADS) {
       const uint32_t p = __ldcg(dpart + c);
       atomicAdd(&S.cnt[p], 1u);
-      atomicAdd(&S.hrec[p], (unsigned long long)__ldcg(dcount + c));
+      smem_add_u64(&S.hrec[p], (unsigned long long)__ldcg(dcount + c));
     }
     __syncthreads();
     for (uint32_t p = threadIdx.x; p < fan; p += THREADS) {
@@ -1262,7 +1429,16 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     // sub-partition scratch.  Whole partitions are packed into each round.
     const uint32_t half = (P.slots / 2) / BUCKET * BUCKET;
     longlong2* scratch = reinterpret_cast<longlong2*>(P.ent + (size_t)half * Ent<ENT>::ES);
-    const uint64_t scratch_recs = ((uint64_t)(P.slots - half) * Ent<ENT>::ES) / REC_BYTES;
+    // the per-block histogram rows of the shared-memory rounds sit at the end of the scratch
+    const uint64_t scratch_bytes = (uint64_t)(P.slots - half) * Ent<ENT>::ES;
+    // (at most a quarter of the scratch; fewer columns make larger sub-partitions)
+    uint64_t hs = 2ull * cc.n < NSUB_MAX ? 2ull * cc.n : NSUB_MAX;
+    const uint64_t hs_fit = scratch_bytes / 4 / ((uint64_t)T.nb * 4);
+    if (hs > hs_fit) hs = hs_fit;
+    const uint32_t hstride = hs > 0 ? (uint32_t)hs : 1u;
+    const uint64_t hbytes = ((uint64_t)T.nb * hstride * 4 + 255) / 256 * 256;
+    const uint64_t scratch_recs = scratch_bytes > hbytes ? (scratch_bytes - hbytes) / REC_BYTES : 0;
+    uint32_t* hrows = reinterpret_cast<uint32_t*>(P.ent + (size_t)half * Ent<ENT>::ES + scratch_recs * REC_BYTES);
     const uint64_t round_cap = scratch_recs < ROUND_CAP_MAX ? scratch_recs : ROUND_CAP_MAX;
     const bool smem_ok = cc.n >= (uint32_t)THREADS && round_cap >= (uint64_t)TILE;
     Level G;
@@ -1285,7 +1461,9 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
           tot += r;
           ++q;
         }
-        if (!smem_round<ENT>(P, T, tm, G, S, cc, src, S.begin[p], S.begin[q], tot, rnd & 1, scratch)) return false;
+        if (!smem_round<ENT>(P, T, tm, G, S, cc, src, S.begin[p], S.begin[q], tot, rnd & 1, scratch, hrows,
+                                 hstride))
+          return false;
         if (threadIdx.x == 0 && T.bid == 0) C->rounds += 1;
         ++rnd;
         tm.lap(T, C, PH_ROUND_AGG);
@@ -1303,6 +1481,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
         }
         adapt_begin_tile(S, cc.n != 0 && P.cache != 0, P.dedup != 0);
         __syncthreads();
+        if (S.flush_tiles >= CACHE_FLUSH_TILES) cache_flush<ENT>(P, cc, S);
         long long k[RPT], v[RPT];
         bool valid[RPT];
 #pragma unroll
