@@ -22,7 +22,17 @@ constexpr int64_t EMPTY_KEY = INT64_MIN;   // empty key slot; this one key value
 constexpr int64_t SKEY_EMPTY = INT64_MIN;  // empty marker of the shared-memory cache
 constexpr int PHASES = 12;                 // phase timers kept by block 0
 constexpr uint32_t NSUB_MAX = 4096;        // sub-partitions of one shared-memory round
-constexpr uint64_t ROUND_CAP_MAX = 8ull << 20;  // records of one shared-memory round (128 MiB of scratch)
+#ifndef AGG_ROUND_CAP_M
+#define AGG_ROUND_CAP_M 8
+#endif
+#ifndef AGG_GTABLE_DIV
+#define AGG_GTABLE_DIV 2
+#endif
+constexpr uint64_t ROUND_CAP_MAX = (uint64_t)AGG_ROUND_CAP_M << 20;  // records of one shared-memory round
+// At recursion levels >= 1 the global table (keys that overflow a block's
+// shared-memory table, partitions too large for a shared-memory round) keeps
+// 1/GTABLE_DIV of the slots; the rest of the entry memory is round scratch.
+constexpr uint32_t GTABLE_DIV = AGG_GTABLE_DIV;
 constexpr uint64_t REC_BYTES = 16;         // spilled record: (int64 key, int64 value)
 // One tile adds at most TILE rows to a partition, so at most one new chunk is
 // opened per partition per tile.

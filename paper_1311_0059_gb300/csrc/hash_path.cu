@@ -149,6 +149,7 @@ struct Smem {
   uint32_t cur[MAX_FAN];   // current staging chunk per partition (NONE = none)
   uint32_t fill[MAX_FAN];  // records in the current chunk (CH when none)
   uint32_t nxt[MAX_FAN];   // chunk opened for this tile's overflow
+  uint32_t pend[MAX_FAN];  // records of the last spilling tile not yet applied to cur/fill
   uint32_t begin[MAX_FAN + 1];
   unsigned long long hrec[MAX_FAN];
   unsigned long long spilled;
@@ -156,7 +157,6 @@ struct Smem {
   uint32_t warp_tot[WARPS];
   uint32_t scan_total;
   uint32_t ok;
-  uint32_t cache_used;
   uint32_t first_spill;
   uint32_t tiles;      // tiles processed by this block (adaptive sampling clock)
   uint32_t flush_tiles;  // tiles since the shared-memory cache was last flushed
@@ -397,44 +397,53 @@ struct Level {
   uint32_t fan_mask;
 };
 
+// The level-0 cache is 4-way set associative: a key may occupy only the four
+// entries of its set (n / 4 sets), so a probe is one 32-byte read and four
+// compares, with no probe loop for the warp to wait on.
+constexpr uint32_t CACHE_WAYS = 4;
+
+__device__ __forceinline__ uint32_t cache_set(const Cache& cc, uint64_t h) {
+  return ((uint32_t)(h >> 16) & (cc.n / CACHE_WAYS - 1)) * CACHE_WAYS;
+}
+
+__device__ __forceinline__ void sh_ld_volatile_s64x2(const long long* p, long long& a, long long& b) {
+  asm volatile("ld.volatile.shared.v2.s64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(sh_addr(p)) : "memory");
+}
+
 // Shared-memory cache probe; true when the key's partial state was updated.
 template <int ENT>
 __device__ __forceinline__ bool cache_hit(const Cache& cc, long long key, uint64_t h, unsigned long long c,
                                           unsigned long long s, long long mn, long long mx) {
   if (cc.n == 0 || key == SKEY_EMPTY) return false;
-  uint32_t idx = (uint32_t)(h >> 16) & (cc.n - 1);
-#pragma unroll 1
-  for (int i = 0; i < 8; ++i) {
-    const long long kk = sh_ld_volatile_s64(cc.key + idx);
-    if (kk == key) {
-      sh_red_add_u32(cc.cnt + idx, (uint32_t)c);
-      smem_add_u64(cc.sum + idx, s);
-      if (Ent<ENT>::MM) {
-        sh_red_min_s64(cc.mn + idx, mn);
-        sh_red_max_s64(cc.mx + idx, mx);
-      }
-      return true;
-    }
-    if (kk == SKEY_EMPTY) return false;
-    idx = (idx + 1) & (cc.n - 1);
+  const uint32_t b = cache_set(cc, h);
+  long long k0, k1, k2, k3;
+  sh_ld_volatile_s64x2(cc.key + b, k0, k1);
+  sh_ld_volatile_s64x2(cc.key + b + 2, k2, k3);
+  const int way = k0 == key ? 0 : k1 == key ? 1 : k2 == key ? 2 : k3 == key ? 3 : -1;
+  if (way < 0) return false;
+  const uint32_t idx = b + (uint32_t)way;
+  sh_red_add_u32(cc.cnt + idx, (uint32_t)c);
+  smem_add_u64(cc.sum + idx, s);
+  if (Ent<ENT>::MM) {
+    sh_red_min_s64(cc.mn + idx, mn);
+    sh_red_max_s64(cc.mx + idx, mx);
   }
-  return false;
+  return true;
 }
 
+// Records a resident key's global slot in a free way of its cache set (first
+// come, first kept; entries are never evicted before a flush).
 __device__ __forceinline__ void cache_insert(const Cache& cc, Smem& S, long long key, uint64_t h, uint32_t slot) {
   if (cc.n == 0 || key == SKEY_EMPTY) return;
-  if (sh_ld_volatile_u32(&S.cache_used) >= cc.n / 2) return;
-  uint32_t idx = (uint32_t)(h >> 16) & (cc.n - 1);
-#pragma unroll 1
-  for (int i = 0; i < 8; ++i) {
-    const long long old = sh_cas_s64(cc.key + idx, SKEY_EMPTY, key);
+  const uint32_t b = cache_set(cc, h);
+#pragma unroll
+  for (uint32_t w = 0; w < CACHE_WAYS; ++w) {
+    const long long old = sh_cas_s64(cc.key + b + w, SKEY_EMPTY, key);
     if (old == SKEY_EMPTY) {
-      cc.slot[idx] = slot;
-      sh_red_add_u32(&S.cache_used, 1u);
+      cc.slot[b + w] = slot;
       return;
     }
     if (old == key) return;
-    idx = (idx + 1) & (cc.n - 1);
   }
 }
 
@@ -457,10 +466,7 @@ __device__ void cache_flush(const HashParams& P, const Cache& cc, Smem& S) {
       cc.mx[i] = INT64_MIN;
     }
   }
-  if (threadIdx.x == 0) {
-    S.cache_used = 0;
-    S.flush_tiles = 0;
-  }
+  if (threadIdx.x == 0) S.flush_tiles = 0;
   __syncthreads();
 }
 
@@ -657,10 +663,26 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
   __syncthreads();
   const uint32_t fan = L.fan_mask + 1;
   const uint32_t dst = L.dst;
+  // Partition p's thread first applies the previous spilling tile's records to
+  // the chunk cursor (deferred to here so that no barrier is needed after the
+  // stores), then takes this tile's count.
   for (uint32_t p = threadIdx.x; p < fan; p += THREADS) {
+    const uint32_t pc = S.pend[p];
+    uint32_t f = S.fill[p];
+    if (pc) {
+      if (f + pc > CH) {
+        S.cur[p] = S.nxt[p];
+        f = f + pc - CH;
+      } else {
+        f += pc;
+      }
+      S.fill[p] = f;
+    }
     const uint32_t c = S.cnt[p];
+    S.cnt[p] = 0;
+    S.pend[p] = c;
     if (c == 0) continue;
-    const uint32_t f = S.fill[p];
+    smem_add_u64(&S.spilled, (unsigned long long)c);
     if (f + c > CH) {  // this tile overflows the current chunk: open a new one
       uint32_t nc = NONE;
       const unsigned long long id = atomicAdd(&P.ctrl->pool_next[dst], 1ull);
@@ -694,31 +716,27 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
     rec.y = v[r];
     __stcs(reinterpret_cast<longlong2*>(P.stg[dst] + ((size_t)chunk * CH + at) * REC_BYTES), rec);
   }
-  __syncthreads();
-  for (uint32_t p = threadIdx.x; p < fan; p += THREADS) {
-    const uint32_t c = S.cnt[p];
-    if (c == 0) continue;
-    const uint32_t f = S.fill[p];
-    if (f + c > CH) {
-      S.cur[p] = S.nxt[p];
-      S.fill[p] = f + c - CH;
-    } else {
-      S.fill[p] = f + c;
-    }
-    S.cnt[p] = 0;
-    smem_add_u64(&S.spilled, (unsigned long long)c);
-  }
-  __syncthreads();
 }
 
 // Closes every open staging chunk of this block (writes its record count).
 __device__ void finalize_chunks(const HashParams& P, Smem& S, uint32_t dst, uint32_t level) {
   __syncthreads();
   for (uint32_t p = threadIdx.x; p < MAX_FAN; p += THREADS) {
-    if (S.cur[p] != NONE) P.dir_count[dst][S.cur[p]] = S.fill[p];
+    uint32_t cur = S.cur[p], f = S.fill[p];
+    const uint32_t pc = S.pend[p];
+    if (pc) {  // the last spilling tile's records
+      if (f + pc > CH) {
+        cur = S.nxt[p];
+        f = f + pc - CH;
+      } else {
+        f += pc;
+      }
+    }
+    if (cur != NONE) P.dir_count[dst][cur] = f;
     S.cur[p] = NONE;
     S.fill[p] = CH;
     S.cnt[p] = 0;
+    S.pend[p] = 0;
   }
   if (threadIdx.x == 0) {
     if (S.spilled) atomicAdd(&P.ctrl->spill_records[level], S.spilled);
@@ -874,51 +892,65 @@ __device__ __forceinline__ void cache_reset_all(const Cache& cc, Smem& S, bool m
       cc.mx[i] = INT64_MIN;
     }
   }
-  if (threadIdx.x == 0) S.cache_used = 0;
 }
 
 // Writes the groups of the shared-memory table to the output and clears it.
+// Each warp takes a contiguous slice of the slots and reserves its output rows
+// with one atomic of its own, so that no block-wide scan is needed; one block
+// barrier at the end keeps the next sub-partition off the table until it is
+// clear.  Returns the groups this thread's warp wrote (lane 0; 0 elsewhere).
 template <int ENT>
-__device__ uint32_t sub_emit(const HashParams& P, const Cache& cc, Smem& S, uint32_t level) {
-  const uint32_t per = cc.n / THREADS;  // consecutive slots per thread
-  const uint32_t i0 = threadIdx.x * per;
-  uint32_t oc = 0;
-  for (uint32_t i = 0; i < per; ++i) oc += cc.key[i0 + i] != SKEY_EMPTY;
-  uint32_t total;
-  const uint32_t off = block_exclusive_scan(oc, total, S);
-  if (threadIdx.x == 0) {
-    S.scan_base = total ? atomicAdd(&P.ctrl->out_count, (unsigned long long)total) : 0ull;
-    if (total) atomicAdd(&P.ctrl->resident_groups[level], (unsigned long long)total);
-  }
-  __syncthreads();
-  unsigned long long pos = S.scan_base + off;
-  for (uint32_t i = 0; i < per; ++i) {
-    const uint32_t j = i0 + i;
-    const long long key = cc.key[j];
-    if (key != SKEY_EMPTY) {
-      if (pos < P.o_cap) {
-        P.o_keys[pos] = key;
-        if (P.o_count) P.o_count[pos] = cc.cnt[j];
-        if (P.o_sum) P.o_sum[pos] = (long long)cc.sum[j];
-        if (Ent<ENT>::MM) {
-          if (P.o_min) P.o_min[pos] = cc.mn[j];
-          if (P.o_max) P.o_max[pos] = cc.mx[j];
+__device__ uint32_t sub_emit(const HashParams& P, const Cache& cc, uint32_t level) {
+  constexpr int SPL = 4;  // slots per lane in one pass of a warp (slices of 32 * SPL slots)
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t slice = cc.n / WARPS;  // multiple of 32 * SPL for n >= 2048; a loop covers the rest
+  uint32_t mine = 0;
+  for (uint32_t b0 = warp * slice; b0 < (warp + 1) * slice; b0 += 32 * SPL) {
+    long long key[SPL];
+    uint32_t occ[SPL], tot = 0;
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) {
+      const uint32_t j = b0 + q * 32 + lane;
+      key[q] = j < (warp + 1) * slice ? cc.key[j] : SKEY_EMPTY;
+      occ[q] = __ballot_sync(FULL_MASK, key[q] != SKEY_EMPTY);
+      tot += __popc(occ[q]);
+    }
+    if (tot == 0) continue;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&P.ctrl->out_count, (unsigned long long)tot);
+    base = __shfl_sync(FULL_MASK, base, 0);
+    mine += tot;
+    uint32_t before = 0;
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) {
+      const uint32_t j = b0 + q * 32 + lane;
+      if (key[q] != SKEY_EMPTY) {
+        const unsigned long long pos = base + before + __popc(occ[q] & lanemask_lt());
+        if (pos < P.o_cap) {
+          P.o_keys[pos] = key[q];
+          if (P.o_count) P.o_count[pos] = cc.cnt[j];
+          if (P.o_sum) P.o_sum[pos] = (long long)cc.sum[j];
+          if (Ent<ENT>::MM) {
+            if (P.o_min) P.o_min[pos] = cc.mn[j];
+            if (P.o_max) P.o_max[pos] = cc.mx[j];
+          }
+        } else {
+          set_status(P.ctrl, AGG_ERR_OUTPUT_CAPACITY);
         }
-      } else {
-        set_status(P.ctrl, AGG_ERR_OUTPUT_CAPACITY);
+        cc.key[j] = SKEY_EMPTY;
+        cc.cnt[j] = 0;
+        cc.sum[j] = 0;
+        if (Ent<ENT>::MM) {
+          cc.mn[j] = INT64_MAX;
+          cc.mx[j] = INT64_MIN;
+        }
       }
-      ++pos;
-    }
-    cc.key[j] = SKEY_EMPTY;
-    cc.cnt[j] = 0;
-    cc.sum[j] = 0;
-    if (Ent<ENT>::MM) {
-      cc.mn[j] = INT64_MAX;
-      cc.mx[j] = INT64_MIN;
+      before += __popc(occ[q]);
     }
   }
+  if (lane == 0 && mine) atomicAdd(&P.ctrl->resident_groups[level], (unsigned long long)mine);
   __syncthreads();
-  return total;
+  return lane == 0 ? mine : 0u;
 }
 
 // Sub-partition of a record within its round (hash bits 16..31, independent of
@@ -1159,13 +1191,11 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
     }
     if (overflow) atomicOr(&C->overflow_used[G.level & 1], 1u);
     __syncthreads();
-    my_groups += sub_emit<ENT>(P, cc, S, G.level);
+    my_groups += sub_emit<ENT>(P, cc, G.level);
     my_recs += hi - lo;
   }
-  if (threadIdx.x == 0 && my_recs) {
-    atomicAdd(&C->lvl_sub_records[par], my_recs);
-    atomicAdd(&C->lvl_sub_groups[par], my_groups);
-  }
+  if (threadIdx.x == 0 && my_recs) atomicAdd(&C->lvl_sub_records[par], my_recs);
+  if (my_groups) atomicAdd(&C->lvl_sub_groups[par], my_groups);  // lane 0 of each warp
   cache_reset_all(cc, S, Ent<ENT>::MM);
   __syncthreads();
   tm.lap(T, C, PH_SUB_AGG);
@@ -1174,8 +1204,8 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
 
 // Restores the entries that served as scratch to the empty state.
 template <int ENT>
-__device__ void restore_scratch(const HashParams& P, const Team& T, uint32_t half) {
-  for (uint64_t s = half + T.bid * (uint64_t)THREADS + threadIdx.x; s < P.slots;
+__device__ void restore_scratch(const HashParams& P, const Team& T, uint32_t gslots) {
+  for (uint64_t s = gslots + T.bid * (uint64_t)THREADS + threadIdx.x; s < P.slots;
        s += (uint64_t)T.nb * THREADS)
     Ent<ENT>::reset(Ent<ENT>::at(P.ent, (uint32_t)s));
 }
@@ -1243,6 +1273,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     S.cnt[p] = 0;
     S.cur[p] = NONE;
     S.fill[p] = CH;
+    S.pend[p] = 0;
     S.hrec[p] = 0;
   }
   for (uint32_t i = threadIdx.x; i < cc.n; i += THREADS) {
@@ -1255,7 +1286,6 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     }
   }
   if (threadIdx.x == 0) {
-    S.cache_used = 0;
     S.spilled = 0;
     S.first_spill = 1;
     S.tiles = 0;
@@ -1423,11 +1453,11 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
       }
     }
     tm.lap(T, C, PH_LISTS);
-    // Rounds.  At levels >= 1 the global table keeps the lower half of the
+    // Rounds.  At levels >= 1 the global table keeps the first 1/GTABLE_DIV of the
     // slots (keys that overflow shared memory, partitions too big for a
     // shared-memory round) and the upper half of the entry memory serves as
     // sub-partition scratch.  Whole partitions are packed into each round.
-    const uint32_t half = (P.slots / 2) / BUCKET * BUCKET;
+    const uint32_t half = (P.slots / GTABLE_DIV) / BUCKET * BUCKET;
     longlong2* scratch = reinterpret_cast<longlong2*>(P.ent + (size_t)half * Ent<ENT>::ES);
     // the per-block histogram rows of the shared-memory rounds sit at the end of the scratch
     const uint64_t scratch_bytes = (uint64_t)(P.slots - half) * Ent<ENT>::ES;
