@@ -10,7 +10,7 @@
  * MIN and MAX are int64 (int32 input values are widened).
  *
  * The work runs under a strictly bounded working-memory budget given at
- * creation (Section 3.2: "a tightly bounded memory budget to each query").
+ * creation (Section 3.2: each query gets its own strict working-memory bound).
  * Groups that do not fit are partitioned, spilled to a staging area and
  * aggregated recursively, in the hybrid-hash style of Section 4.3 with the
  * Pre-Partitioning policy of Section 4.3.4 (the table is filled first; once it
