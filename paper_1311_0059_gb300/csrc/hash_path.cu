@@ -349,17 +349,29 @@ __device__ __forceinline__ uint32_t key_tag(uint64_t h) {
   return t ? t : 1u;
 }
 
+// First slot of a key's probe order inside its bucket (hash bits 27..31).  Each
+// key walks the bucket from its own starting slot, wrapping around, so that
+// concurrent inserts of different keys do not all race for slot 0.
+__device__ __forceinline__ uint32_t key_start(uint64_t h) { return (uint32_t)(h >> 27) & (BUCKET - 1); }
+
+// Candidate mask in a key's probe order: bit j stands for slot (start + j) mod 32.
+__device__ __forceinline__ uint32_t rotate_cand(uint32_t cand, uint32_t start) {
+  return __funnelshift_r(cand, cand, start);
+}
+
 // Finds or claims the slot of `key` in its bucket, given the bucket's candidate
-// mask and the key word of its first candidate slot (`k_first`, loaded by the
-// caller so that the loads of several rows overlap).  A key may live only in
-// its bucket, in the first slot that was free when it arrived: the candidates
-// are visited in slot order; a free slot is claimed by a 64-bit CAS; a slot
-// taken meanwhile by another key is passed.  Returns the slot when the key is
-// (now) resident, -1 when the bucket holds 32 other keys (the key spills).
+// mask in the key's probe order (`cand`, see rotate_cand) and the key word of
+// its first candidate slot (`k_first`, loaded by the caller so that the loads
+// of several rows overlap).  A key may live only in its bucket, in the first
+// slot of its probe order that was free when it arrived: the candidates are
+// visited in that order; a free slot is claimed by a 64-bit CAS; a slot taken
+// meanwhile by another key is passed.  Every insert of the same key walks the
+// same order, so a key is never claimed twice.  Returns the slot when the key
+// is (now) resident, -1 when the bucket holds 32 other keys (the key spills).
 // *claimed is set when this call inserted it.
 template <int ENT>
-__device__ long long probe_table(const HashParams& P, uint32_t b, uint32_t cand, long long key, uint32_t tag,
-                                 uint32_t& claimed, long long k_first) {
+__device__ long long probe_table(const HashParams& P, uint32_t b, uint32_t cand, uint32_t start, long long key,
+                                 uint32_t tag, uint32_t& claimed, long long k_first) {
   if (key == EMPTY_KEY) {  // the empty marker value itself: side slot, always resident
     uint8_t* tb = reinterpret_cast<uint8_t*>(P.tags) + P.slots;
     if (__ldcg(tb) == 0) __stcg(tb, (uint8_t)0x80);
@@ -367,7 +379,7 @@ __device__ long long probe_table(const HashParams& P, uint32_t b, uint32_t cand,
   }
   bool first = true;
   while (cand) {
-    const uint32_t i = __ffs(cand) - 1;
+    const uint32_t i = (__ffs(cand) - 1 + start) & (BUCKET - 1);
     cand &= cand - 1;
     const uint32_t slot = b * BUCKET + i;
     long long* kp = reinterpret_cast<long long*>(Ent<ENT>::at(P.ent, slot));
@@ -608,7 +620,9 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     cand[r] = 0;
-    if (need[r] && k[r] != EMPTY_KEY) cand[r] = bucket_candidates(P, home_bucket(h[r], L.s_act), key_tag(h[r]) * 0x01010101u);
+    if (need[r] && k[r] != EMPTY_KEY)
+      cand[r] = rotate_cand(bucket_candidates(P, home_bucket(h[r], L.s_act), key_tag(h[r]) * 0x01010101u),
+                            key_start(h[r]));
   }
   // key word of every row's first candidate slot, all loads in flight together
   long long kf[RPT];
@@ -616,7 +630,8 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
   for (int r = 0; r < RPT; ++r) {
     kf[r] = EMPTY_KEY;
     if (cand[r]) {
-      const uint32_t slot = home_bucket(h[r], L.s_act) * BUCKET + (__ffs(cand[r]) - 1);
+      const uint32_t slot =
+          home_bucket(h[r], L.s_act) * BUCKET + ((__ffs(cand[r]) - 1 + key_start(h[r])) & (BUCKET - 1));
       kf[r] = __ldcg(reinterpret_cast<const long long*>(Ent<ENT>::at(P.ent, slot)));
     }
   }
@@ -628,7 +643,7 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
     if (!need[r]) continue;
     uint32_t claimed = 0;
     const long long slot =
-        probe_table<ENT>(P, home_bucket(h[r], L.s_act), cand[r], k[r], key_tag(h[r]), claimed, kf[r]);
+        probe_table<ENT>(P, home_bucket(h[r], L.s_act), cand[r], key_start(h[r]), k[r], key_tag(h[r]), claimed, kf[r]);
     if (slot >= 0) {
       Ent<ENT>::add(Ent<ENT>::at(P.ent, (uint32_t)slot), P.ops, 1ull, (unsigned long long)v[r], v[r], v[r]);
       if (cache_ins) cache_insert(cc, S, k[r], h[r], (uint32_t)slot);
