@@ -72,6 +72,7 @@ struct alignas(128) Ctrl {
   unsigned long long lvl_sub_records[2];  // records aggregated in shared memory (by round parity)
   unsigned long long lvl_sub_groups[2];   // groups they formed (keys-per-record estimate)
   unsigned int overflow_used[2];          // a key of the level (by parity) went to the global table
+  unsigned int sub_next[2];               // pass C: sub-partitions claimed so far (by round parity)
   // ---- snapshot of the last completed run
   unsigned long long last_n_rows;
   unsigned long long last_n_groups;

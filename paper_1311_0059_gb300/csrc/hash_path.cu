@@ -164,6 +164,7 @@ struct Smem {
   uint32_t use_dedup;
   uint32_t st_rows, st_hits, st_dups;
   unsigned long long tile_q[2];  // level-0 tiles claimed by this block (current, next) by iteration parity
+  uint32_t sub_q[2];            // pass C: sub-partitions claimed by this block, by iteration parity
   uint32_t tl_chunk[TLIST];     // staged tiles of a round pass: chunk id
   uint32_t tl_count[TLIST];     // and its record count
 };
@@ -1096,6 +1097,8 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
   for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) __stcg(myrow + i, hist[i]);
   if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
 
+  // this round's pass-C claim counter (its parity was last used two rounds ago)
+  if (T.bid == 0 && threadIdx.x == 0) C->sub_next[par] = 0;
   // ---- scan: a block takes 32 columns at a time; its warps split the team's
   // rows, sum their share, exchange the sums, then write the exclusive offsets
   {
@@ -1181,10 +1184,16 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
   tm.lap(T, C, PH_SUB_SCATTER);
 
   // ---- pass C: whole sub-partitions aggregated in shared memory
+  // Sub-partitions are claimed dynamically (one ahead), so that blocks that
+  // drew small ones take more.
   cache_reset_all(cc, S, Ent<ENT>::MM);
-  __syncthreads();
+  if (threadIdx.x == 0) S.sub_q[0] = atomicAdd(&C->sub_next[par], 1u);
   unsigned long long my_recs = 0, my_groups = 0;
-  for (uint32_t sbi = T.bid; sbi < nsub; sbi += T.nb) {
+  for (uint32_t it = 0;; ++it) {
+    __syncthreads();  // sub_q[it & 1] is visible; the table is clear
+    const uint32_t sbi = S.sub_q[it & 1];
+    if (sbi >= nsub) break;
+    if (threadIdx.x == 0) S.sub_q[(it + 1) & 1] = atomicAdd(&C->sub_next[par], 1u);
     uint32_t lo = __ldcg(&C->sub_base[par][sbi]), hi = __ldcg(&C->sub_base[par][sbi + 1]);
     if (hi > tot || lo > hi) {  // inconsistent offsets: report, never read past the scratch
       if (threadIdx.x == 0) set_status(C, AGG_ERR_INTERNAL);
