@@ -35,6 +35,7 @@ namespace {
 constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
 constexpr int WARPS = THREADS / 32;
 constexpr uint32_t TLIST = 128;  // tiles of a round pass whose chunk ids are staged at once
+constexpr uint32_t A_TILES = 4;  // tiles whose keys one step of the count pass loads together
 
 __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
   k ^= k >> 33;
@@ -492,7 +493,7 @@ constexpr uint32_t CACHE_FLUSH_TILES = 1u << 20;
 // Per-block adaptive features: every SAMPLE_PERIOD tiles, SAMPLE_TILES tiles
 // run with warp dedup and the shared-memory cache both on and count how many
 // rows each saves; the block keeps a feature on while it pays.
-constexpr uint32_t SAMPLE_PERIOD = 32, SAMPLE_TILES = 2;
+constexpr uint32_t SAMPLE_PERIOD = 128, SAMPLE_TILES = 2;
 
 __device__ __forceinline__ void adapt_begin_tile(Smem& S, bool cache_allowed, bool dedup_allowed) {
   if (threadIdx.x == 0) {
@@ -1074,13 +1075,13 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
   for (uint32_t i = threadIdx.x; i < nsub; i += THREADS) hist[i] = 0;
   for (uint64_t tb = T.bid; tb < ntiles; tb += (uint64_t)TLIST * T.nb) {
     const uint32_t nj = stage_tiles(T, S, list, dcount, c0, ntiles, tb);
-    if (threadIdx.x < 2 && threadIdx.x < nj) prefetch_staged(P, src, S, threadIdx.x);
-    for (uint32_t j = 0; j < nj; j += 2) {  // two tiles per step: 2 * RPT loads in flight per thread
-      if (threadIdx.x < 2 && j + 2 + threadIdx.x < nj) prefetch_staged(P, src, S, j + 2 + threadIdx.x);
-      long long k[2 * RPT];
-      bool ok[2 * RPT];
+    if (threadIdx.x < A_TILES && threadIdx.x < nj) prefetch_staged(P, src, S, threadIdx.x);
+    for (uint32_t j = 0; j < nj; j += A_TILES) {  // A_TILES tiles per step: A_TILES * RPT loads in flight
+      if (threadIdx.x < A_TILES && j + A_TILES + threadIdx.x < nj) prefetch_staged(P, src, S, j + A_TILES + threadIdx.x);
+      long long k[A_TILES * RPT];
+      bool ok[A_TILES * RPT];
 #pragma unroll
-      for (int r = 0; r < 2 * RPT; ++r) {  // keys only
+      for (int r = 0; r < A_TILES * RPT; ++r) {  // keys only
         const uint32_t jj = j + (uint32_t)(r / RPT);
         const uint32_t off = (uint32_t)(r % RPT) * THREADS + threadIdx.x;
         ok[r] = jj < nj && off < S.tl_count[jj];
@@ -1089,7 +1090,7 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
                      : 0;
       }
 #pragma unroll
-      for (int r = 0; r < 2 * RPT; ++r)
+      for (int r = 0; r < A_TILES * RPT; ++r)
         if (ok[r]) sh_red_add_u32(&hist[sub_of(fmix64((uint64_t)k[r] ^ G.seed), (uint32_t)nsub)], 1u);
     }
   }
