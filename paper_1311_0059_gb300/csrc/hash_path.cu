@@ -84,10 +84,6 @@ __device__ __forceinline__ void set_status(Ctrl* c, agg_status s) {
   atomicOr(&c->status_bits, 1ull << (int)s);
 }
 
-// 4 bits of a byte-wise 0xFF/0x00 mask word, one per byte.
-__device__ __forceinline__ uint32_t byte_mask_bits(uint32_t m) {
-  return ((m >> 7) & 1u) | ((m >> 14) & 2u) | ((m >> 21) & 4u) | ((m >> 28) & 8u);
-}
 
 // Adds v to a 64-bit word in shared memory, exactly modulo 2^64, with 32-bit
 // atomics: the low word takes the low half of v and reports the carry it
@@ -322,9 +318,14 @@ struct Ent {
   }
 };
 
-// Candidate slots of a bucket, in probe order: tag byte equal to the key's tag,
-// or still zero (free, or claimed a moment ago with its tag not yet written).
-// The bucket's 32 tag bytes are one 32-byte sector, read with one 256-bit load.
+// Candidate slots of a bucket: tag byte equal to the key's tag, or still zero
+// (free, or claimed a moment ago with its tag not yet written).  The bucket's
+// 32 tag bytes are one 32-byte sector, read with one 256-bit load and tested
+// four bytes at a time with an exact zero-byte test: bit 7 of each byte of
+// ((v & 0x7F..) + 0x7F..) | v is set iff that byte of v is non-zero.  The mask
+// is built in word-interleaved order (bit 8b + i stands for byte b of tag word
+// i, slot cand_slot(8b + i) = 4i + b), which needs no gathering of bits; the
+// probe order only has to be fixed per key, not ascending.
 __device__ __forceinline__ uint32_t bucket_candidates(const HashParams& P, uint32_t b, uint32_t tag4) {
   unsigned long long q0, q1, q2, q3;
   asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
@@ -333,13 +334,18 @@ __device__ __forceinline__ uint32_t bucket_candidates(const HashParams& P, uint3
   const unsigned long long q[4] = {q0, q1, q2, q3};
   uint32_t cand = 0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const uint32_t lo = (uint32_t)q[i], hi = (uint32_t)(q[i] >> 32);
-    cand |= byte_mask_bits(__vcmpeq4(lo, tag4) | __vcmpeq4(lo, 0u)) << (8 * i);
-    cand |= byte_mask_bits(__vcmpeq4(hi, tag4) | __vcmpeq4(hi, 0u)) << (8 * i + 4);
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t w = (i & 1) ? (uint32_t)(q[i >> 1] >> 32) : (uint32_t)q[i >> 1];
+    const uint32_t x = w ^ tag4;
+    const uint32_t nz_x = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
+    const uint32_t nz_w = ((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w;
+    cand |= (~(nz_x & nz_w) & 0x80808080u) >> (7 - i);
   }
   return cand;
 }
+
+// Slot within its bucket of candidate bit p (see bucket_candidates).
+__device__ __forceinline__ uint32_t cand_slot(uint32_t p) { return 4 * (p & 7) + (p >> 3); }
 
 __device__ __forceinline__ uint32_t home_bucket(uint64_t h, uint32_t s_act) {
   return (uint32_t)(((h >> 32) * (uint64_t)(s_act / BUCKET)) >> 32);
@@ -356,7 +362,8 @@ __device__ __forceinline__ uint32_t key_tag(uint64_t h) {
 // concurrent inserts of different keys do not all race for slot 0.
 __device__ __forceinline__ uint32_t key_start(uint64_t h) { return (uint32_t)(h >> 27) & (BUCKET - 1); }
 
-// Candidate mask in a key's probe order: bit j stands for slot (start + j) mod 32.
+// Candidate mask in a key's probe order: bit j stands for candidate position
+// (start + j) mod 32, that is slot cand_slot((start + j) mod 32).
 __device__ __forceinline__ uint32_t rotate_cand(uint32_t cand, uint32_t start) {
   return __funnelshift_r(cand, cand, start);
 }
@@ -381,7 +388,7 @@ __device__ long long probe_table(const HashParams& P, uint32_t b, uint32_t cand,
   }
   bool first = true;
   while (cand) {
-    const uint32_t i = (__ffs(cand) - 1 + start) & (BUCKET - 1);
+    const uint32_t i = cand_slot((__ffs(cand) - 1 + start) & (BUCKET - 1));
     cand &= cand - 1;
     const uint32_t slot = b * BUCKET + i;
     long long* kp = reinterpret_cast<long long*>(Ent<ENT>::at(P.ent, slot));
@@ -633,7 +640,7 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
     kf[r] = EMPTY_KEY;
     if (cand[r]) {
       const uint32_t slot =
-          home_bucket(h[r], L.s_act) * BUCKET + ((__ffs(cand[r]) - 1 + key_start(h[r])) & (BUCKET - 1));
+          home_bucket(h[r], L.s_act) * BUCKET + cand_slot((__ffs(cand[r]) - 1 + key_start(h[r])) & (BUCKET - 1));
       kf[r] = __ldcg(reinterpret_cast<const long long*>(Ent<ENT>::at(P.ent, slot)));
     }
   }
