@@ -432,16 +432,21 @@ __device__ __forceinline__ void sh_ld_volatile_s64x2(const long long* p, long lo
 }
 
 // Shared-memory cache probe; true when the key's partial state was updated.
+// *free_way tells whether the set had a free way (worth an insert later).
 template <int ENT>
 __device__ __forceinline__ bool cache_hit(const Cache& cc, long long key, uint64_t h, unsigned long long c,
-                                          unsigned long long s, long long mn, long long mx) {
+                                          unsigned long long s, long long mn, long long mx, bool& free_way) {
+  free_way = false;
   if (cc.n == 0 || key == SKEY_EMPTY) return false;
   const uint32_t b = cache_set(cc, h);
   long long k0, k1, k2, k3;
   sh_ld_volatile_s64x2(cc.key + b, k0, k1);
   sh_ld_volatile_s64x2(cc.key + b + 2, k2, k3);
   const int way = k0 == key ? 0 : k1 == key ? 1 : k2 == key ? 2 : k3 == key ? 3 : -1;
-  if (way < 0) return false;
+  if (way < 0) {
+    free_way = k0 == SKEY_EMPTY || k1 == SKEY_EMPTY || k2 == SKEY_EMPTY || k3 == SKEY_EMPTY;
+    return false;
+  }
   const uint32_t idx = b + (uint32_t)way;
   sh_red_add_u32(cc.cnt + idx, (uint32_t)c);
   smem_add_u64(cc.sum + idx, s);
@@ -529,7 +534,7 @@ __device__ __forceinline__ void adapt_end_tile(Smem& S, bool cache_allowed, bool
 template <int ENT>
 __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, const Cache& cc, long long (&k)[RPT],
                                  long long (&v)[RPT], const uint64_t (&h)[RPT], const bool (&need)[RPT],
-                                 uint64_t tile_row0, bool cache_ins);
+                                 const bool (&cfree)[RPT], uint64_t tile_row0, bool cache_ins);
 
 // Aggregates up to RPT rows per thread (block-uniform call), then spills the
 // rows whose keys are not resident.  `tile_row0` orders level-0 tiles.
@@ -541,6 +546,7 @@ __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const
   const bool use_dedup = S.use_dedup;
   const bool sampling = (S.tiles % SAMPLE_PERIOD) < SAMPLE_TILES;
   bool need[RPT];
+  bool cfree[RPT];  // the row's cache set had a free way when probed (or was not probed)
   uint64_t h[RPT];  // each row's hash under this level's seed, computed once
   uint32_t hits = 0, dups = 0;
 
@@ -548,6 +554,7 @@ __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     need[r] = valid[r];
+    cfree[r] = true;
     h[r] = fmix64((uint64_t)k[r] ^ L.seed);
   }
   if (use_cache) {
@@ -571,21 +578,27 @@ __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const
             const long long ov = __shfl_sync(FULL_MASK, v[r], src);
             if (src != (int)lane) {
               gs += (unsigned long long)ov;
-              gmn = ov < gmn ? ov : gmn;
-              gmx = ov > gmx ? ov : gmx;
+              if (Ent<ENT>::MM) {
+                gmn = ov < gmn ? ov : gmn;
+                gmx = ov > gmx ? ov : gmx;
+              }
             }
           }
           gc = gsize;
         }
-        if (val && lane == leader) dups += gsize - 1;
+        if (sampling && val && lane == leader) dups += gsize - 1;
       }
-      bool hit = false;
+      bool hit = false, cf = true;
       if (val && lane == leader) {
-        hit = cache_hit<ENT>(cc, k[r], h[r], gc, gs, gmn, gmx);
-        hits += hit ? (uint32_t)gc : 0u;
+        hit = cache_hit<ENT>(cc, k[r], h[r], gc, gs, gmn, gmx, cf);
+        if (sampling) hits += hit ? (uint32_t)gc : 0u;
       }
-      if (use_dedup) hit = __shfl_sync(FULL_MASK, hit, leader);
+      if (use_dedup) {
+        hit = __shfl_sync(FULL_MASK, hit, leader);
+        cf = __shfl_sync(FULL_MASK, cf, leader);
+      }
       need[r] = val && !hit;
+      cfree[r] = cf;
     }
   } else if (sampling && use_dedup) {
     // no cache: dedup only measured (global updates stay per row)
@@ -612,7 +625,7 @@ __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const
     }
   }
 
-  global_and_spill<ENT>(P, L, S, cc, k, v, h, need, tile_row0, use_cache || sampling);
+  global_and_spill<ENT>(P, L, S, cc, k, v, h, need, cfree, tile_row0, use_cache || sampling);
 }
 
 // Updates the global table for every row with need[r] set (claiming slots for
@@ -622,7 +635,7 @@ __device__ void process_rows(const HashParams& P, const Level& L, Smem& S, const
 template <int ENT>
 __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, const Cache& cc, long long (&k)[RPT],
                                  long long (&v)[RPT], const uint64_t (&h)[RPT], const bool (&need)[RPT],
-                                 uint64_t tile_row0, bool cache_ins) {
+                                 const bool (&cfree)[RPT], uint64_t tile_row0, bool cache_ins) {
   const uint32_t lane = threadIdx.x & 31;
   // ---- global table: bucket tags of every remaining row first, then resolve
   uint32_t cand[RPT];
@@ -655,7 +668,7 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
         probe_table<ENT>(P, home_bucket(h[r], L.s_act), cand[r], key_start(h[r]), k[r], key_tag(h[r]), claimed, kf[r]);
     if (slot >= 0) {
       Ent<ENT>::add(Ent<ENT>::at(P.ent, (uint32_t)slot), P.ops, 1ull, (unsigned long long)v[r], v[r], v[r]);
-      if (cache_ins) cache_insert(cc, S, k[r], h[r], (uint32_t)slot);
+      if (cache_ins && cfree[r]) cache_insert(cc, S, k[r], h[r], (uint32_t)slot);
     } else {
       sp[r] = true;
       any_sp = true;
@@ -1230,7 +1243,7 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
         need[r] = in[r] && !sub_upsert<ENT>(cc, k[r], h[r], v[r]);
         overflow |= need[r];
       }
-      global_and_spill<ENT>(P, G, S, cc, k, v, h, need, 0, false);
+      global_and_spill<ENT>(P, G, S, cc, k, v, h, need, in, 0, false);
     }
     if (overflow) atomicOr(&C->overflow_used[G.level & 1], 1u);
     __syncthreads();
