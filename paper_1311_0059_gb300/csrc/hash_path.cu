@@ -1364,8 +1364,11 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     // ahead so that the next tile can be staged in L2 while this one runs.
     const uint64_t ntiles = (P.n + TILE - 1) / TILE;
     if (threadIdx.x == 0) S.tile_q[0] = atomicAdd(&C->tile_next, 1ull);
+    adapt_begin_tile(S, cc.n != 0 && P.cache != 0, P.dedup != 0);
     for (uint32_t it = 0;; ++it) {
-      __syncthreads();  // tile_q[it & 1] is visible; every thread is done with the previous tile
+      // tile_q[it & 1] and this tile's feature flags are visible; every thread
+      // is done with the previous tile
+      __syncthreads();
       const uint64_t t = S.tile_q[it & 1];
       if (t >= ntiles) break;
       if (S.flush_tiles >= CACHE_FLUSH_TILES) cache_flush<ENT>(P, cc, S);
@@ -1382,8 +1385,6 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
                         (uint32_t)(nrows * (VT == AGG_I64 ? 8 : 4)));
         }
       }
-      adapt_begin_tile(S, cc.n != 0 && P.cache != 0, P.dedup != 0);
-      __syncthreads();
       long long k[RPT], v[RPT];
       bool valid[RPT];
 #pragma unroll
@@ -1423,6 +1424,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
       }
       process_rows<ENT>(P, L, S, cc, k, v, valid, row0);
       adapt_end_tile(S, cc.n != 0 && P.cache != 0, P.dedup != 0);
+      adapt_begin_tile(S, cc.n != 0 && P.cache != 0, P.dedup != 0);  // flags of the next tile
     }
     cache_flush<ENT>(P, cc, S);
     finalize_chunks(P, S, 0, 0);
