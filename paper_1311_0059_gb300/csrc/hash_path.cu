@@ -675,13 +675,9 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
     }
   }
 
-  if (!__syncthreads_or(any_sp)) return;
-  if (threadIdx.x == 0 && L.level == 0 && S.first_spill) {
-    S.first_spill = 0;
-    atomicMin(&P.ctrl->rows_at_full, (unsigned long long)tile_row0);
-  }
-
-  // ---- spill: warp-aggregated ranks per partition
+  // ---- spill: warp-aggregated ranks per partition, taken before the block
+  // knows whether any row spills (a tile without spills adds nothing to the
+  // counters), so that the vote below also serves as the barrier after them
   uint32_t part[RPT], rank[RPT];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
@@ -697,7 +693,11 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
       rank[r] = base + __popc(pm & lanemask_lt());
     }
   }
-  __syncthreads();
+  if (!__syncthreads_or(any_sp)) return;
+  if (threadIdx.x == 0 && L.level == 0 && S.first_spill) {
+    S.first_spill = 0;
+    atomicMin(&P.ctrl->rows_at_full, (unsigned long long)tile_row0);
+  }
   const uint32_t fan = L.fan_mask + 1;
   const uint32_t dst = L.dst;
   // Partition p's thread first applies the previous spilling tile's records to
