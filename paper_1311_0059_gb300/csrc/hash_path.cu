@@ -829,13 +829,34 @@ __device__ void emit_one(const HashParams& P, uint8_t* e, unsigned long long pos
   Ent<ENT>::reset(e);
 }
 
+// Clears the whole shared-memory table.
+__device__ __forceinline__ void cache_reset_all(const Cache& cc, Smem& S, bool mm) {
+  for (uint32_t i = threadIdx.x; i < cc.n; i += THREADS) {
+    cc.key[i] = SKEY_EMPTY;
+    cc.cnt[i] = 0;
+    cc.sum[i] = 0;
+    if (mm) {
+      cc.mn[i] = INT64_MAX;
+      cc.mx[i] = INT64_MIN;
+    }
+  }
+}
+
 // Writes every occupied slot of the active table (and the side slot) to the
-// output and resets them.
+// output and resets them.  The table is cut into segments of THREADS * 4 tag
+// words; a block scan over each segment reserves its output rows with one
+// atomic.  When the shared-memory table is idle (it is at every call) and large
+// enough, the segment's occupied slots are first listed in it, and the block's
+// threads then emit the list in stride, so that no thread serialises the
+// entries of a dense stretch of the table; the idle table is cleared after.
 template <int ENT>
-__device__ void emit_table(const HashParams& P, const Team& T, uint32_t s_act, uint32_t level, Smem& S) {
+__device__ void emit_table(const HashParams& P, const Team& T, const Cache& cc, uint32_t s_act, uint32_t level,
+                           Smem& S) {
   const uint32_t words = s_act / 4;
   constexpr uint32_t WPT = 4;  // tag words per thread
   const uint32_t seg_words = THREADS * WPT;
+  uint32_t* list = reinterpret_cast<uint32_t*>(cc.key);  // key and sum (and min, max) arrays are contiguous
+  const bool use_list = (uint64_t)cc.n * (Ent<ENT>::MM ? 8u : 4u) >= (uint64_t)seg_words * 4;
   for (uint32_t seg = T.bid; (uint64_t)seg * seg_words < words; seg += T.nb) {
     const uint32_t w0 = seg * seg_words + threadIdx.x * WPT;
     uint32_t tw[WPT];
@@ -858,6 +879,22 @@ __device__ void emit_table(const HashParams& P, const Team& T, uint32_t s_act, u
       S.scan_base = total ? atomicAdd(&P.ctrl->out_count, (unsigned long long)total) : 0ull;
       if (total) atomicAdd(&P.ctrl->resident_groups[level], (unsigned long long)total);
     }
+    if (use_list) {
+      uint32_t o = off;
+#pragma unroll
+      for (uint32_t q = 0; q < WPT; ++q) {
+        if (tw[q] == 0) continue;
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j)
+          if ((tw[q] >> (8 * j)) & 0xFFu) list[o++] = (w0 + q) * 4 + j;
+        __stcg(P.tags + w0 + q, 0u);
+      }
+      __syncthreads();  // list and scan_base complete
+      const unsigned long long base = S.scan_base;
+      for (uint32_t i = threadIdx.x; i < total; i += THREADS) emit_one<ENT>(P, Ent<ENT>::at(P.ent, list[i]), base + i);
+      __syncthreads();  // list free for the next segment
+      continue;
+    }
     __syncthreads();
     unsigned long long pos = S.scan_base + off;
 #pragma unroll
@@ -871,6 +908,10 @@ __device__ void emit_table(const HashParams& P, const Team& T, uint32_t s_act, u
       }
       __stcg(P.tags + w0 + q, 0u);
     }
+    __syncthreads();
+  }
+  if (use_list) {  // the shared-memory table served as the list: clear it
+    cache_reset_all(cc, S, Ent<ENT>::MM);
     __syncthreads();
   }
   // the side slot of the empty-marker key
@@ -928,18 +969,6 @@ __device__ __forceinline__ bool sub_upsert(const Cache& cc, long long key, uint6
     g = (g + 4) & (cc.n - 1);
   }
   return false;
-}
-
-__device__ __forceinline__ void cache_reset_all(const Cache& cc, Smem& S, bool mm) {
-  for (uint32_t i = threadIdx.x; i < cc.n; i += THREADS) {
-    cc.key[i] = SKEY_EMPTY;
-    cc.cnt[i] = 0;
-    cc.sum[i] = 0;
-    if (mm) {
-      cc.mn[i] = INT64_MAX;
-      cc.mx[i] = INT64_MIN;
-    }
-  }
 }
 
 // Writes the groups of the shared-memory table to the output and clears it.
@@ -1432,7 +1461,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
     tm.lap(T, C, PH_L0_WAIT);
     const unsigned long long spilled = ld_relaxed_u64(&C->pool_next[0]);
-    emit_table<ENT>(P, T, L.s_act, 0, S);
+    emit_table<ENT>(P, T, cc, L.s_act, 0, S);
     tm.lap(T, C, PH_L0_EMIT);
     if (spilled == 0) {
       total.lap(T, C, PH_TOTAL);
@@ -1585,7 +1614,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
       tm.lap(T, C, PH_ROUND_AGG);
       if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
       tm.lap(T, C, PH_ROUND_WAIT);
-      emit_table<ENT>(P, T, half, level, S);
+      emit_table<ENT>(P, T, cc, half, level, S);
       if (threadIdx.x == 0 && T.bid == 0) C->rounds += 1;
       tm.lap(T, C, PH_ROUND_EMIT);
       if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
@@ -1595,7 +1624,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     finalize_chunks(P, S, dst, level);
     if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
     tm.lap(T, C, PH_ROUND_WAIT);
-    if (ld_acquire_u32(&C->overflow_used[level & 1])) emit_table<ENT>(P, T, half, level, S);
+    if (ld_acquire_u32(&C->overflow_used[level & 1])) emit_table<ENT>(P, T, cc, half, level, S);
     tm.lap(T, C, PH_ROUND_EMIT);
     if (ld_relaxed_u64(&C->pool_next[dst]) == 0) {
       restore_scratch<ENT>(P, T, half);
