@@ -85,7 +85,8 @@ typedef struct agg_tuning {
                               two 256..4096 (default 2048); 1 disables the cache */
   uint32_t fan_out;        /* spill partitions per level, power of two 16..256;
                               0 = planner (Eq. 1 with fudge factor, Section 4.3) */
-  uint32_t warp_dedup;     /* 0 = default (on), 1 = on, 2 = off */
+  uint32_t warp_dedup;     /* warp-level combining of equal keys (__match_any_sync) before the
+                              shared-memory table: 0 = default (off), 1 = on, 2 = off */
   uint32_t reserved;
   double fudge;            /* fudge factor F of Eq. 1 (default 1.2, Section 6.7) */
 } agg_tuning;

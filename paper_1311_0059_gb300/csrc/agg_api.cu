@@ -95,7 +95,7 @@ agg_tuning effective(const agg_tuning* t) {
   e.max_load_factor = (t && t->max_load_factor > 0) ? t->max_load_factor : DEFAULT_LF;
   e.smem_entries = (t && t->smem_entries) ? t->smem_entries : DEFAULT_NS;
   e.fan_out = t ? t->fan_out : 0;
-  e.warp_dedup = (t && t->warp_dedup) ? t->warp_dedup : 1;
+  e.warp_dedup = (t && t->warp_dedup) ? t->warp_dedup : 2;  // off unless asked for
   e.fudge = (t && t->fudge > 0) ? t->fudge : DEFAULT_FUDGE;
   return e;
 }
@@ -825,7 +825,7 @@ agg_status agg_batch_create(const agg_spec* spec, const agg_batch_item* items, u
       p.s_act0 = (uint32_t)plan[i].s_act0;
       p.ns = tune.smem_entries;
       p.cache = 1;
-      p.dedup = 1;
+      p.dedup = tune.warp_dedup == 1 ? 1 : 0;
       p.timeout_ns = TIMEOUT_NS;
     }
   }
@@ -1070,7 +1070,7 @@ agg_status server_launch(agg_server* s, ServerQuery& sq, int slot) {
   p.s_act0 = active_slots(q.expected_groups ? q.expected_groups : (n ? n : 1), p.lf, slots);
   p.ns = s->tune.smem_entries;
   p.cache = 1;
-  p.dedup = 1;
+  p.dedup = s->tune.warp_dedup == 1 ? 1 : 0;
   p.timeout_ns = TIMEOUT_NS;
   KernelInfo ki = s->ki;
   ki.blocks = (int)team;

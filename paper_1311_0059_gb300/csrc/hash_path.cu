@@ -675,23 +675,15 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
     }
   }
 
-  // ---- spill: warp-aggregated ranks per partition, taken before the block
-  // knows whether any row spills (a tile without spills adds nothing to the
-  // counters), so that the vote below also serves as the barrier after them
+  // ---- spill: ranks per partition from one shared-memory atomic per row
+  // (cheaper than warp aggregation with __match_any_sync), taken before the
+  // block knows whether any row spills (a tile without spills adds nothing to
+  // the counters), so that the vote below also serves as the barrier after them
   uint32_t part[RPT], rank[RPT];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     part[r] = (uint32_t)(h[r] >> 8) & L.fan_mask;
-    const uint32_t vm = __ballot_sync(FULL_MASK, sp[r]);
-    rank[r] = 0;
-    if (sp[r]) {
-      const uint32_t pm = __match_any_sync(vm, part[r]);
-      const int ldr = __ffs(pm) - 1;
-      uint32_t base = 0;
-      if ((int)lane == ldr) base = sh_atom_add_u32(&S.cnt[part[r]], (uint32_t)__popc(pm));
-      base = __shfl_sync(pm, base, ldr);
-      rank[r] = base + __popc(pm & lanemask_lt());
-    }
+    rank[r] = sp[r] ? sh_atom_add_u32(&S.cnt[part[r]], 1u) : 0u;
   }
   if (!__syncthreads_or(any_sp)) return;
   if (threadIdx.x == 0 && L.level == 0 && S.first_spill) {
@@ -1213,14 +1205,10 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
     for (int r = 0; r < RPT; ++r) sb[r] = ok[r] ? sub_of(fmix64((uint64_t)k[r] ^ G.seed), (uint32_t)nsub) : 0u;
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      const uint32_t vm = __ballot_sync(FULL_MASK, ok[r]);
+      // one shared-memory atomic per record: lanes rarely share one of the
+      // round's ~thousand sub-partitions, and __match_any_sync costs more
       if (ok[r]) {
-        const uint32_t pm = __match_any_sync(vm, sb[r]);
-        const int ldr = __ffs(pm) - 1;
-        uint32_t b0 = 0;
-        if ((int)lane == ldr) b0 = sh_atom_add_u32(&cur[sb[r]], (uint32_t)__popc(pm));
-        b0 = __shfl_sync(pm, b0, ldr);
-        const uint64_t at = (uint64_t)b0 + __popc(pm & lanemask_lt());
+        const uint64_t at = sh_atom_add_u32(&cur[sb[r]], 1u);
         longlong2 rec;
         rec.x = k[r];
         rec.y = v[r];

@@ -152,7 +152,7 @@ extern "C" agg_status agg_run_noalloc(const agg_spec* spec, const int64_t* d_key
   p.s_act0 = NA_SLOTS;
   p.ns = 2048;
   p.cache = 1;
-  p.dedup = 1;
+  p.dedup = 0;
   p.timeout_ns = 4000000000ull;
   if (hash_launch(ent, spec->value_type, p, d->ki[ent][spec->value_type], s) != cudaSuccess) {
     cudaGetLastError();

@@ -134,7 +134,8 @@ def test_zipf_workload_scaled(oracle):
 
 
 @pytest.mark.parametrize("tune", [dict(), dict(max_load_factor=0.9), dict(smem_entries=1), dict(smem_entries=256),
-                                  dict(warp_dedup=2), dict(fan_out=256), dict(max_load_factor=0.2, fan_out=16)])
+                                  dict(warp_dedup=1), dict(warp_dedup=2), dict(fan_out=256),
+                                  dict(max_load_factor=0.2, fan_out=16)])
 def test_result_invariant_under_tuning(oracle, tune):
     from paper_1311_0059_gb300 import agg_tuning
     w = dg.Workload("tune", n=1_500_000, domain=400_000, dist="zipf", zipf_s=0.8)
