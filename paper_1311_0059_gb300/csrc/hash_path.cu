@@ -149,7 +149,7 @@ struct Smem {
   uint32_t pend[MAX_FAN];  // records of the last spilling tile not yet applied to cur/fill
   uint32_t begin[MAX_FAN + 1];
   unsigned long long hrec[MAX_FAN];
-  unsigned long long spilled;
+  unsigned long long pspill[MAX_FAN];  // rows spilled to each partition at this level (by its fan-loop thread)
   unsigned long long scan_base;
   uint32_t warp_tot[WARPS];
   uint32_t scan_total;
@@ -711,7 +711,7 @@ __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, c
     S.cnt[p] = 0;
     S.pend[p] = c;
     if (c == 0) continue;
-    smem_add_u64(&S.spilled, (unsigned long long)c);
+    S.pspill[p] += c;
     if (f + c > CH) {  // this tile overflows the current chunk: open a new one
       uint32_t nc = NONE;
       const unsigned long long id = atomicAdd(&P.ctrl->pool_next[dst], 1ull);
@@ -766,10 +766,8 @@ __device__ void finalize_chunks(const HashParams& P, Smem& S, uint32_t dst, uint
     S.fill[p] = CH;
     S.cnt[p] = 0;
     S.pend[p] = 0;
-  }
-  if (threadIdx.x == 0) {
-    if (S.spilled) atomicAdd(&P.ctrl->spill_records[level], S.spilled);
-    S.spilled = 0;
+    if (S.pspill[p]) atomicAdd(&P.ctrl->spill_records[level], S.pspill[p]);
+    S.pspill[p] = 0;
   }
   __syncthreads();
 }
@@ -1227,8 +1225,10 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
   cache_reset_all(cc, S, Ent<ENT>::MM);
   if (threadIdx.x == 0) S.sub_q[0] = atomicAdd(&C->sub_next[par], 1u);
   unsigned long long my_recs = 0, my_groups = 0;
+  __syncthreads();
+  // each iteration ends with sub_emit's barrier, which also publishes the
+  // sub-partition claimed for the next iteration
   for (uint32_t it = 0;; ++it) {
-    __syncthreads();  // sub_q[it & 1] is visible; the table is clear
     const uint32_t sbi = S.sub_q[it & 1];
     if (sbi >= nsub) break;
     if (threadIdx.x == 0) S.sub_q[(it + 1) & 1] = atomicAdd(&C->sub_next[par], 1u);
@@ -1263,7 +1263,7 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
       global_and_spill<ENT>(P, G, S, cc, k, v, h, need, in, 0, false);
     }
     if (overflow) atomicOr(&C->overflow_used[G.level & 1], 1u);
-    __syncthreads();
+    if (lo == hi) __syncthreads();  // else the last tile's vote in global_and_spill ordered every upsert before the emit
     my_groups += sub_emit<ENT>(P, cc, G.level);
     my_recs += hi - lo;
   }
@@ -1347,6 +1347,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     S.cur[p] = NONE;
     S.fill[p] = CH;
     S.pend[p] = 0;
+    S.pspill[p] = 0;
     S.hrec[p] = 0;
   }
   for (uint32_t i = threadIdx.x; i < cc.n; i += THREADS) {
@@ -1359,7 +1360,6 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     }
   }
   if (threadIdx.x == 0) {
-    S.spilled = 0;
     S.first_spill = 1;
     S.tiles = 0;
     S.flush_tiles = 0;
