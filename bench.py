@@ -396,7 +396,8 @@ def run_ours(args):
         e2e_rows = sum_over_ranks(float(w.n * ek), world, dev)
         line["e2e"] = {"value": e2e_rows / dt, "unit": "rows/s", "h2d_bytes_per_step": in_b,
                        "d2h_bytes_per_step": int(ng.value) * 8 * (1 + nagg) + 8, "steps": ek,
-                       "api": "agg_run_host (pinned host buffers)"}
+                       "api": "agg_run_host on pinned host buffers: the kernel reads the input from and writes the "
+                              "result rows into host memory over the host link, inside the timed region"}
 
     if not args.no_cpu and rank == 0:
         rows = args.cpu_rows or default_cpu_rows(w)

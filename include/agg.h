@@ -171,10 +171,16 @@ agg_status agg_reserve(agg_handle* h, uint64_t max_rows);
 agg_status agg_run(agg_handle* h, const int64_t* d_keys, const void* d_vals, uint64_t n,
                    const agg_output* out, void* stream);
 
-/* Same group-by on host buffers: copies h_keys/h_vals to device buffers owned
- * by the handle, runs, waits, and copies the n_groups result rows back into the
- * host arrays of h_out (capacity counted in rows).  Pinned host memory gives
- * the full copy bandwidth.  *n_groups receives the group count.  Synchronous. */
+/* Same group-by on host buffers; writes the n_groups result rows into the host
+ * arrays of h_out (capacity counted in rows) and *n_groups.  Synchronous.
+ * Hash path, when the device can address every buffer (pinned memory, or
+ * pageable memory on a host with coherent device access such as Grace over
+ * NVLink-C2C): the kernel reads the input from host memory and writes the
+ * result rows straight into h_out, so that both transfers overlap its work.
+ * Otherwise (and on the sort path) the input is copied to device buffers owned
+ * by the handle and the result is copied back after the run; pinned host memory
+ * gives the full copy bandwidth.  Errors as agg_run and agg_sync;
+ * AGG_ERR_OUTPUT_CAPACITY when n_groups exceeds h_out->capacity. */
 agg_status agg_run_host(agg_handle* h, const int64_t* h_keys, const void* h_vals, uint64_t n,
                         const agg_output* h_out, uint64_t* n_groups, void* stream);
 

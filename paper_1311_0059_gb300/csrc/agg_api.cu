@@ -238,6 +238,10 @@ agg_status status_from_bits(unsigned long long bits) {
   return bits ? AGG_ERR_INTERNAL : AGG_OK;
 }
 
+agg_status hash_enqueue(agg_handle* h, const int64_t* d_keys, const void* d_vals, uint64_t n, const agg_output* out,
+                        cudaStream_t s, bool host_input);
+const void* device_view(const void* p, int device);
+
 }  // namespace
 
 extern "C" {
@@ -422,7 +426,19 @@ agg_status agg_run(agg_handle* h, const int64_t* d_keys, const void* d_vals, uin
     h->ran = true;
     return st;
   }
+  return hash_enqueue(h, d_keys, d_vals, n, out, s, false);
+}
 
+}  // extern "C"
+
+namespace {
+
+// Enqueues the hash-path kernel.  Pointers are checked by the caller; they are
+// device memory, or host memory the device can address when host_input is set
+// (the kernel then streams the input over the host link and does not stage
+// input tiles in L2 with bulk prefetches).
+agg_status hash_enqueue(agg_handle* h, const int64_t* d_keys, const void* d_vals, uint64_t n, const agg_output* out,
+                        cudaStream_t s, bool host_input) {
   const uint32_t fan = plan_fan(&h->spec, h->tune, n, h->budget, h->es);
   if (!h->stg_mem[0] || n > h->reserved_rows || fan > h->reserved_fan) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -466,6 +482,7 @@ agg_status agg_run(agg_handle* h, const int64_t* d_keys, const void* d_vals, uin
   p.ns = h->tune.smem_entries > 1 ? h->tune.smem_entries : DEFAULT_NS;
   p.cache = h->tune.smem_entries != 1;
   p.dedup = h->tune.warp_dedup == 1 ? 1 : 0;
+  p.no_prefetch = host_input ? 1 : 0;
   p.timeout_ns = TIMEOUT_NS;
   if (hash_launch(h->ent_kind, h->spec.value_type, p, h->ki, s) != cudaSuccess) {
     cudaGetLastError();
@@ -476,6 +493,31 @@ agg_status agg_run(agg_handle* h, const int64_t* d_keys, const void* d_vals, uin
   h->ran = true;
   return AGG_OK;
 }
+
+// The address through which the device reaches host buffer p: the device
+// pointer of pinned (registered) memory, or p itself when the device accesses
+// pageable memory coherently (a Grace host over NVLink-C2C).  nullptr when the
+// device cannot reach p.
+const void* device_view(const void* p, int device) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+  int pageable = 0;
+  if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return pageable ? p : nullptr;
+}
+
+}  // namespace
+
+extern "C" {
 
 agg_status agg_sync(agg_handle* h, uint64_t* n_groups_host) {
   if (!h) return AGG_ERR_INVALID_ARG;
@@ -554,6 +596,54 @@ agg_status agg_run_host(agg_handle* h, const int64_t* h_keys, const void* h_vals
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t vb = h->spec.value_type == AGG_I64 ? 8 : 4;
   const uint64_t rows = n ? n : 1;
+  const bool need_vals = (h->spec.ops & ~(uint32_t)AGG_COUNT) != 0;
+  if (n > 0 && need_vals && !h_vals) return AGG_ERR_INVALID_ARG;
+
+  // Direct mode (hash path): when the device can address every host buffer,
+  // the kernel streams the input from host memory and writes the result rows
+  // into the host arrays over the host link, overlapping both transfers with
+  // its own work instead of copying before and after it.
+  if (h->spec.path == AGG_PATH_HASH && n > 0) {
+    const void* dk = device_view(h_keys, h->device);
+    const void* dv = h_vals ? device_view(h_vals, h->device) : nullptr;
+    agg_output dout{};
+    dout.keys = static_cast<int64_t*>(const_cast<void*>(device_view(h_out->keys, h->device)));
+    const uint32_t ops = h->spec.ops;
+    dout.count = (ops & AGG_COUNT) && h_out->count
+                     ? static_cast<uint64_t*>(const_cast<void*>(device_view(h_out->count, h->device)))
+                     : nullptr;
+    dout.sum = (ops & AGG_SUM) && h_out->sum ? static_cast<int64_t*>(const_cast<void*>(device_view(h_out->sum, h->device)))
+                                             : nullptr;
+    dout.min = (ops & AGG_MIN) && h_out->min ? static_cast<int64_t*>(const_cast<void*>(device_view(h_out->min, h->device)))
+                                             : nullptr;
+    dout.max = (ops & AGG_MAX) && h_out->max ? static_cast<int64_t*>(const_cast<void*>(device_view(h_out->max, h->device)))
+                                             : nullptr;
+    const bool direct = dk && (!h_vals || dv) && dout.keys && (!(ops & AGG_COUNT) || !h_out->count || dout.count) &&
+                        (!(ops & AGG_SUM) || !h_out->sum || dout.sum) && (!(ops & AGG_MIN) || !h_out->min || dout.min) &&
+                        (!(ops & AGG_MAX) || !h_out->max || dout.max) &&
+                        (reinterpret_cast<uintptr_t>(dk) & 7) == 0 &&
+                        (!dv || (reinterpret_cast<uintptr_t>(dv) & (vb - 1)) == 0);
+    if (direct) {
+      if (!h->out_buf) {
+        if (cudaMalloc(&h->out_buf, 64) != cudaSuccess) {
+          cudaGetLastError();
+          return AGG_ERR_OOM;
+        }
+      }
+      dout.capacity = h_out->capacity;
+      dout.d_n_groups = static_cast<uint64_t*>(h->out_buf) + (h->out_cap ? h->out_cap * 5 : 0);
+      agg_status st = hash_enqueue(h, static_cast<const int64_t*>(dk), dv, n, &dout, s, true);
+      if (st != AGG_OK) return st;
+      if (cudaMemcpyAsync(h->ng_host, dout.d_n_groups, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return AGG_ERR_CUDA;
+      uint64_t ng = 0;
+      st = agg_sync(h, &ng);
+      ng = h->ng_host[0];
+      if (n_groups) *n_groups = ng;
+      if (st != AGG_OK) return st;
+      return ng > h_out->capacity ? AGG_ERR_OUTPUT_CAPACITY : AGG_OK;
+    }
+  }
   if (rows > h->in_cap) {
     if (h->in_buf) cudaFree(h->in_buf);
     h->in_buf = nullptr;

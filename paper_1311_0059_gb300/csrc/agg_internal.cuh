@@ -115,6 +115,7 @@ struct HashParams {
   uint32_t ns;         // shared-memory table entries (power of two)
   uint32_t dedup;      // warp-level key dedup on/off
   uint32_t cache;      // shared-memory cache of resident groups on/off
+  uint32_t no_prefetch;  // input in host memory: no bulk L2 prefetch of input tiles
   uint64_t timeout_ns; // bounded waits give up after this long
 };
 

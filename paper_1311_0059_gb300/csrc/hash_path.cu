@@ -1393,7 +1393,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
       if (threadIdx.x == 0) {
         const uint64_t nt = atomicAdd(&C->tile_next, 1ull);
         S.tile_q[(it + 1) & 1] = nt;
-        if (P.vec_ok && nt < ntiles) {  // stage the next tile in L2
+        if (P.vec_ok && !P.no_prefetch && nt < ntiles) {  // stage the next tile in L2
           const uint64_t nr0 = nt * TILE;
           const uint64_t nrows = P.n - nr0 < (uint64_t)TILE ? P.n - nr0 : (uint64_t)TILE;
           prefetch_l2(P.keys + nr0, (uint32_t)(nrows * 8));

@@ -247,3 +247,51 @@ def test_spill_200m_50m_full_size_sampled(oracle):
 def test_zipf_500m_10m_full_size_sampled(oracle):
     st = _sampled_full_size(oracle, dg.ZIPF_500M_10M)
     assert st["levels"] == 1
+
+
+def _run_host_pinned(g, keys, vals, capacity):
+    """agg_run_host on pinned host tensors (the path the end-to-end bench takes)."""
+    import ctypes
+
+    import torch
+    from paper_1311_0059_gb300._abi import agg_output
+    hk = torch.from_numpy(keys).pin_memory()
+    hv = torch.from_numpy(vals).pin_memory()
+    out = {f: torch.empty(max(capacity, 1), dtype=torch.int64).pin_memory() for f in ("keys", "count", "sum", "min", "max")}
+    ho = agg_output(keys=out["keys"].data_ptr(), count=out["count"].data_ptr(), sum=out["sum"].data_ptr(),
+                    min=out["min"].data_ptr(), max=out["max"].data_ptr(), capacity=capacity, d_n_groups=None)
+    ng = ctypes.c_uint64()
+    st = g.lib.agg_run_host(g.h, ctypes.c_void_p(hk.data_ptr()), ctypes.c_void_p(hv.data_ptr()), keys.size,
+                            ctypes.byref(ho), ctypes.byref(ng), None)
+    res = {f: t.numpy()[:min(ng.value, capacity)] for f, t in out.items()}
+    return st, ng.value, res
+
+
+@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("vd", [np.int64, np.int32])
+def test_run_host_pinned_spilling(oracle, path, vd):
+    # pinned host buffers: the hash path reads the input and writes the result
+    # in host memory directly; the sort path copies
+    from paper_1311_0059_gb300 import AGG_I32, AGG_I64
+    from paper_1311_0059_gb300.groupby import GroupBy
+    keys, vals = rand_case(21 + path, 900_000, 400_000, vdtype=vd)
+    with GroupBy(MB, value_type=AGG_I32 if vd == np.int32 else AGG_I64, path=path) as g:
+        st, ng, res = _run_host_pinned(g, keys, vals, keys.size)
+        assert st == 0
+        if path == 0:
+            assert g.stats()["levels"] >= 2
+    assert_parity(canon(res), oracle_expected(oracle, keys, vals), what=f"path={path}")
+
+
+def test_run_host_pinned_output_capacity(oracle):
+    from paper_1311_0059_gb300 import _abi
+    from paper_1311_0059_gb300.groupby import GroupBy
+    keys, vals = rand_case(23, 100_000, 5_000)
+    exp = oracle_expected(oracle, keys, vals)
+    with GroupBy(8 * MB) as g:
+        st, ng, _ = _run_host_pinned(g, keys, vals, exp["keys"].size - 1)
+        assert st == _abi.AGG_ERR_OUTPUT_CAPACITY
+        assert ng == exp["keys"].size
+        st, ng, res = _run_host_pinned(g, keys, vals, exp["keys"].size)  # the handle is usable again
+        assert st == 0 and ng == exp["keys"].size
+    assert_parity(canon(res), exp)
