@@ -1,28 +1,31 @@
 // Hash path of the budgeted group-by: one persistent cooperative kernel per run.
 //
-// Level 0 streams the input once (Section 4.3, Phase 1).  Each row's key is
-// hashed with the MurmurHash3 64-bit finaliser under a per-level seed (Section
-// 6.7).  Duplicates inside a warp are combined first (match_any + shuffles),
-// then a per-block shared-memory cache of resident groups absorbs hot keys, and
+// Level 0 streams the input once (Section 4.3, Phase 1), in tiles claimed
+// dynamically by the blocks.  Each row's key is hashed once with the
+// MurmurHash3 64-bit finaliser under a per-level seed (Section 6.7).  A
+// per-block, 4-way set-associative shared-memory cache of resident groups
+// absorbs hot keys (optionally after combining equal keys inside a warp), and
 // the remaining updates go to the global open-addressing table with 64-bit
 // atomics.  The table follows the Pre-Partitioning policy (Section 4.3.4):
 // every group that finds room in the table before the table is full is
 // resident and completes in place; a group that finds no room is spilled, and
 // it is spilled whole.  Spilled rows are radix-partitioned on hash bits into
-// staging chunks (the run files of Section 4.3) with warp-aggregated cursors.
-// After the pass the table is emitted and reset.  Spilled partitions are then
-// processed level by level (Phase 2) with fresh seeds; small partitions are
-// packed into one table round (partition tuning, Section 4.3.3).  Phases are
-// separated by grid barriers whose waits are bounded.
+// staging chunks (the run files of Section 4.3), ranked by shared-memory
+// atomics.  After the pass the table is emitted and reset.  Spilled partitions
+// are then processed level by level (Phase 2) with fresh seeds; partitions are
+// packed into rounds (partition tuning, Section 4.3.3), and each round is
+// split into sub-partitions that one block aggregates in shared memory.
+// Phases are separated by grid barriers whose waits are bounded.
 //
 // Table and residency.  Slots form buckets of 32; a key may live only in its
-// hash bucket, in the first slot that was free when it arrived.  A key slot
-// changes once per round, from EMPTY to a key, by a 64-bit atomicCAS, so "k is
-// absent and its bucket holds 32 other keys" can never become false later in
-// the round: such a key spills consistently, and a key is never both resident
-// and spilled.  "Full" (Section 3.2: no new group fits) is therefore judged per
-// bucket.  A tag byte per slot (0x80 | 7 hash bits, written after the claim) is
-// a compact filter kept in L2: a probe reads its bucket's 32 tags in one 32-byte
+// hash bucket, in the first slot of its own probe order (a rotation chosen by
+// hash bits) that was free when it arrived.  A key slot changes once per
+// round, from EMPTY to a key, by a 64-bit atomicCAS, so "k is absent and its
+// bucket holds 32 other keys" can never become false later in the round: such
+// a key spills consistently, and a key is never both resident and spilled.
+// "Full" (Section 3.2: no new group fits) is therefore judged per bucket.  A
+// tag byte per slot (8 hash bits, never zero, written after the claim) is a
+// compact filter kept in L2: a probe reads its bucket's 32 tags in one 32-byte
 // sector and reads keys only where a tag matches or is still zero.  The key
 // value that marks an empty slot (INT64_MIN) is kept in a dedicated side slot.
 #include <cstdio>
@@ -636,7 +639,6 @@ template <int ENT>
 __device__ void global_and_spill(const HashParams& P, const Level& L, Smem& S, const Cache& cc, long long (&k)[RPT],
                                  long long (&v)[RPT], const uint64_t (&h)[RPT], const bool (&need)[RPT],
                                  const bool (&cfree)[RPT], uint64_t tile_row0, bool cache_ins) {
-  const uint32_t lane = threadIdx.x & 31;
   // ---- global table: bucket tags of every remaining row first, then resolve
   uint32_t cand[RPT];
 #pragma unroll
@@ -1530,12 +1532,12 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     tm.lap(T, C, PH_LISTS);
     // Rounds.  At levels >= 1 the global table keeps the first 1/GTABLE_DIV of the
     // slots (keys that overflow shared memory, partitions too big for a
-    // shared-memory round) and the upper half of the entry memory serves as
+    // shared-memory round) and the rest of the entry memory serves as
     // sub-partition scratch.  Whole partitions are packed into each round.
-    const uint32_t half = (P.slots / GTABLE_DIV) / BUCKET * BUCKET;
-    longlong2* scratch = reinterpret_cast<longlong2*>(P.ent + (size_t)half * Ent<ENT>::ES);
+    const uint32_t gslots = (P.slots / GTABLE_DIV) / BUCKET * BUCKET;
+    longlong2* scratch = reinterpret_cast<longlong2*>(P.ent + (size_t)gslots * Ent<ENT>::ES);
     // the per-block histogram rows of the shared-memory rounds sit at the end of the scratch
-    const uint64_t scratch_bytes = (uint64_t)(P.slots - half) * Ent<ENT>::ES;
+    const uint64_t scratch_bytes = (uint64_t)(P.slots - gslots) * Ent<ENT>::ES;
     // (at most a quarter of the scratch; fewer columns make larger sub-partitions)
     uint64_t hs = 2ull * cc.n < NSUB_MAX ? 2ull * cc.n : NSUB_MAX;
     const uint64_t hs_fit = scratch_bytes / 4 / ((uint64_t)T.nb * 4);
@@ -1543,13 +1545,13 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     const uint32_t hstride = hs > 0 ? (uint32_t)hs : 1u;
     const uint64_t hbytes = ((uint64_t)T.nb * hstride * 4 + 255) / 256 * 256;
     const uint64_t scratch_recs = scratch_bytes > hbytes ? (scratch_bytes - hbytes) / REC_BYTES : 0;
-    uint32_t* hrows = reinterpret_cast<uint32_t*>(P.ent + (size_t)half * Ent<ENT>::ES + scratch_recs * REC_BYTES);
+    uint32_t* hrows = reinterpret_cast<uint32_t*>(P.ent + (size_t)gslots * Ent<ENT>::ES + scratch_recs * REC_BYTES);
     const uint64_t round_cap = scratch_recs < ROUND_CAP_MAX ? scratch_recs : ROUND_CAP_MAX;
     const bool smem_ok = cc.n >= (uint32_t)THREADS && round_cap >= (uint64_t)TILE;
     Level G;
     G.level = level;
     G.seed = level_seed(P.seed, level);
-    G.s_act = half;
+    G.s_act = gslots;
     G.dst = dst;
     G.fan_mask = fan - 1;
     uint32_t rnd = 0;
@@ -1602,7 +1604,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
       tm.lap(T, C, PH_ROUND_AGG);
       if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
       tm.lap(T, C, PH_ROUND_WAIT);
-      emit_table<ENT>(P, T, cc, half, level, S);
+      emit_table<ENT>(P, T, cc, gslots, level, S);
       if (threadIdx.x == 0 && T.bid == 0) C->rounds += 1;
       tm.lap(T, C, PH_ROUND_EMIT);
       if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
@@ -1612,10 +1614,10 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     finalize_chunks(P, S, dst, level);
     if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
     tm.lap(T, C, PH_ROUND_WAIT);
-    if (ld_acquire_u32(&C->overflow_used[level & 1])) emit_table<ENT>(P, T, cc, half, level, S);
+    if (ld_acquire_u32(&C->overflow_used[level & 1])) emit_table<ENT>(P, T, cc, gslots, level, S);
     tm.lap(T, C, PH_ROUND_EMIT);
     if (ld_relaxed_u64(&C->pool_next[dst]) == 0) {
-      restore_scratch<ENT>(P, T, half);
+      restore_scratch<ENT>(P, T, gslots);
       total.lap(T, C, PH_TOTAL);
       final_step(P, T, level + 1);
       return true;
