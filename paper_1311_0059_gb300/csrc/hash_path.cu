@@ -98,18 +98,6 @@ __device__ __forceinline__ void set_status(Ctrl* c, agg_status s) {
 // atomic on shared memory is far slower than a shared one).
 __device__ __forceinline__ uint32_t sh_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ long long sh_ld_volatile_s64(const long long* p) {
-  long long v;
-  asm volatile("ld.volatile.shared.s64 %0, [%1];" : "=l"(v) : "r"(sh_addr(p)) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ uint32_t sh_ld_volatile_u32(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(sh_addr(p)) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ long long sh_cas_s64(long long* p, long long cmp, long long val) {
   long long old;
   asm volatile("atom.shared.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "r"(sh_addr(p)), "l"(cmp), "l"(val) : "memory");
