@@ -332,8 +332,13 @@ def run_ours(args):
     # measured spill vs the Pre-Partitioning cost model (Section 5.3.4)
     k_cap = stats["table_capacity"]
     pred = predicted_spill_records(w.n, k_cap, n_groups)
+    # the model again with K = the groups the level-0 table actually held (full
+    # buckets hold more than the planned capacity max_load_factor * slots)
+    k_res = stats["resident_groups"][0]
+    pred_res = predicted_spill_records(w.n, k_res, n_groups)
     spill = {"measured_records_level0": stats["spill_records"][0], "measured_bytes_total": spill_b,
              "model_records_level0": pred, "model_bytes_level0": pred * 16, "K": k_cap, "G_t": n_groups,
+             "K_resident_level0": k_res, "model_records_level0_K_resident": pred_res,
              "levels": stats["levels"], "rounds": stats["rounds"], "fan_out": stats["fan_out"]}
 
     line = {"metric": "group-by rows/s (hash path, HBM-resident input)", "value": value, "unit": "rows/s",
