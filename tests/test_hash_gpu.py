@@ -295,3 +295,45 @@ def test_run_host_pinned_output_capacity(oracle):
         st, ng, res = _run_host_pinned(g, keys, vals, exp["keys"].size)  # the handle is usable again
         assert st == 0 and ng == exp["keys"].size
     assert_parity(canon(res), exp)
+
+
+def test_run_host_count_only_without_values(oracle):
+    # COUNT needs no values: the direct mode runs with h_vals = NULL
+    import ctypes
+
+    import torch
+    from paper_1311_0059_gb300 import AGG_COUNT
+    from paper_1311_0059_gb300._abi import agg_output
+    from paper_1311_0059_gb300.groupby import GroupBy
+    keys, vals = rand_case(31, 500_000, 200_000)
+    exp = oracle_expected(oracle, keys, vals)
+    with GroupBy(MB, ops=AGG_COUNT) as g:
+        hk = torch.from_numpy(keys).pin_memory()
+        ok_ = torch.empty(keys.size, dtype=torch.int64).pin_memory()
+        oc = torch.empty(keys.size, dtype=torch.int64).pin_memory()
+        ho = agg_output(keys=ok_.data_ptr(), count=oc.data_ptr(), sum=None, min=None, max=None, capacity=keys.size,
+                        d_n_groups=None)
+        ng = ctypes.c_uint64()
+        st = g.lib.agg_run_host(g.h, ctypes.c_void_p(hk.data_ptr()), None, keys.size, ctypes.byref(ho),
+                                ctypes.byref(ng), None)
+        assert st == 0 and ng.value == exp["keys"].size
+    got = canon({"keys": ok_.numpy()[:ng.value], "count": oc.numpy()[:ng.value]})
+    assert_parity(got, exp, AGG_COUNT)
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_run_host_pageable_both_paths(oracle, path):
+    from paper_1311_0059_gb300.groupby import GroupBy
+    keys, vals = rand_case(32 + path, 300_000, 120_000)
+    with GroupBy(MB, path=path) as g:
+        got = canon(g.run_host(keys, vals))
+        empty = g.run_host(keys[:0], vals[:0])
+    assert_parity(got, oracle_expected(oracle, keys, vals), what=f"path={path}")
+    assert empty["keys"].size == 0
+
+
+def test_run_host_pinned_empty_input(oracle):
+    from paper_1311_0059_gb300.groupby import GroupBy
+    with GroupBy(MB) as g:
+        st, ng, _ = _run_host_pinned(g, np.zeros(0, np.int64), np.zeros(0, np.int64), 1)
+    assert st == 0 and ng == 0
