@@ -160,7 +160,9 @@ def kernel_source_hash() -> str:
 
 def recorded_traffic(workload_name: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+    the current kernel sources (else None).  An entry lists the source hashes it
+    holds for: the one it was captured on, plus later ones whose changes leave
+    the captured kernel's code and its launch unchanged (each named in _note)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -168,7 +170,7 @@ def recorded_traffic(workload_name: str):
     except (OSError, ValueError):
         return None
     ent = rec.get(workload_name)
-    if not ent or ent.get("kernel_source_hash") != kernel_source_hash():
+    if not ent or kernel_source_hash() not in ent.get("kernel_source_hashes", []):
         return None
     return ent.get("dram_bytes_per_launch")
 

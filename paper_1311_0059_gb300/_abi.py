@@ -41,7 +41,7 @@ class agg_spec(ctypes.Structure):
 
 class agg_tuning(ctypes.Structure):
     _fields_ = [("max_load_factor", ctypes.c_double), ("smem_entries", ctypes.c_uint32),
-                ("fan_out", ctypes.c_uint32), ("warp_dedup", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("fan_out", ctypes.c_uint32), ("warp_dedup", ctypes.c_uint32), ("wait_limit_us", ctypes.c_uint32),
                 ("fudge", ctypes.c_double)]
 
 

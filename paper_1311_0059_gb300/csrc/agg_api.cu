@@ -97,6 +97,7 @@ agg_tuning effective(const agg_tuning* t) {
   e.fan_out = t ? t->fan_out : 0;
   e.warp_dedup = (t && t->warp_dedup) ? t->warp_dedup : 2;  // off unless asked for
   e.fudge = (t && t->fudge > 0) ? t->fudge : DEFAULT_FUDGE;
+  e.wait_limit_us = t ? t->wait_limit_us : 0;
   return e;
 }
 
@@ -483,7 +484,7 @@ agg_status hash_enqueue(agg_handle* h, const int64_t* d_keys, const void* d_vals
   p.cache = h->tune.smem_entries != 1;
   p.dedup = h->tune.warp_dedup == 1 ? 1 : 0;
   p.no_prefetch = host_input ? 1 : 0;
-  p.timeout_ns = TIMEOUT_NS;
+  p.timeout_ns = h->tune.wait_limit_us ? 1000ull * h->tune.wait_limit_us : TIMEOUT_NS;
   if (hash_launch(h->ent_kind, h->spec.value_type, p, h->ki, s) != cudaSuccess) {
     cudaGetLastError();
     return AGG_ERR_CUDA;
