@@ -88,8 +88,9 @@ typedef struct agg_tuning {
   uint32_t warp_dedup;     /* warp-level combining of equal keys (__match_any_sync) before the
                               shared-memory table: 0 = default (off), 1 = on, 2 = off */
   uint32_t wait_limit_us;  /* limit of every bounded device-side wait (grid barriers), in
-                              microseconds; 0 = 4 s.  A wait that runs out ends the run with
-                              AGG_ERR_TIMEOUT (agg_sync) and the handle is rebuilt */
+                              microseconds, at most 60,000,000 (60 s); 0 = 4 s.  A wait that
+                              runs out ends the run with AGG_ERR_TIMEOUT (agg_sync) and the
+                              handle is rebuilt */
   double fudge;            /* fudge factor F of Eq. 1 (default 1.2, Section 6.7) */
 } agg_tuning;
 

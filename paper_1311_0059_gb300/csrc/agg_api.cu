@@ -73,6 +73,7 @@ constexpr double DEFAULT_LF = 0.5;
 constexpr uint32_t DEFAULT_NS = 2048;
 constexpr double DEFAULT_FUDGE = 1.2;
 constexpr uint64_t TIMEOUT_NS = 4000000000ull;
+constexpr uint32_t MAX_WAIT_LIMIT_US = 60000000u;  // a stuck run holds the GPU for at most a minute
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -109,6 +110,7 @@ bool valid_tuning(const agg_tuning* t) {
   }
   if (t->fan_out && (t->fan_out < 16 || t->fan_out > 256 || (t->fan_out & (t->fan_out - 1)))) return false;
   if (t->warp_dedup > 2) return false;
+  if (t->wait_limit_us > MAX_WAIT_LIMIT_US) return false;
   if (t->fudge < 0 || t->fudge > 16) return false;
   return true;
 }

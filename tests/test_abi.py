@@ -63,3 +63,19 @@ def test_plan_is_host_only_and_follows_the_budget(lib):
     with pytest.raises(_abi.AggError) as e:
         gb.plan(1 << 20, 10, bad)
     assert e.value.status == _abi.AGG_ERR_INVALID_ARG
+
+
+def test_tuning_limits_are_checked_on_the_host(lib):
+    from paper_1311_0059_gb300 import groupby as gb, _abi
+    spec = gb.make_spec(ops=15, value_type=_abi.AGG_I64)
+    ok = [_abi.agg_tuning(), _abi.agg_tuning(wait_limit_us=1), _abi.agg_tuning(wait_limit_us=60_000_000),
+          _abi.agg_tuning(smem_entries=1), _abi.agg_tuning(fan_out=256, warp_dedup=1, max_load_factor=0.95)]
+    bad = [_abi.agg_tuning(wait_limit_us=60_000_001), _abi.agg_tuning(smem_entries=512 + 256),
+           _abi.agg_tuning(fan_out=8), _abi.agg_tuning(warp_dedup=3), _abi.agg_tuning(max_load_factor=0.96),
+           _abi.agg_tuning(fudge=-1.0)]
+    for t in ok:
+        gb.plan(64 << 20, 1000, spec, t)
+    for t in bad:
+        with pytest.raises(_abi.AggError) as e:
+            gb.plan(64 << 20, 1000, spec, t)
+        assert e.value.status == _abi.AGG_ERR_INVALID_ARG
