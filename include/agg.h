@@ -230,8 +230,11 @@ typedef struct agg_batch agg_batch;
  * blocks longest-first; every team owns working memory large enough for the
  * largest budget among its instances (each instance uses at most its own
  * budget of it, one instance at a time) and staging for those that may spill.
- * Allocates everything the runs need.  Errors: AGG_ERR_INVALID_ARG,
- * AGG_ERR_BUDGET_TOO_SMALL (an item's budget), AGG_ERR_OOM, AGG_ERR_CUDA. */
+ * Allocates everything the runs need.  Errors: AGG_ERR_INVALID_ARG (also an
+ * item whose input or output arrays are not device memory, whose values are
+ * missing while SUM, MIN or MAX is asked for, or whose keys or values are not
+ * aligned to their element size), AGG_ERR_BUDGET_TOO_SMALL (an item's budget),
+ * AGG_ERR_OOM, AGG_ERR_CUDA. */
 agg_status agg_batch_create(const agg_spec* spec, const agg_batch_item* items, uint32_t count,
                             const agg_batch_tuning* t, agg_batch** out);
 
@@ -290,7 +293,10 @@ typedef struct agg_server agg_server;
  * spec.ops and spec.value_type apply to every query. */
 agg_status agg_server_create(const agg_spec* spec, size_t pool_bytes, uint32_t max_active, agg_server** out);
 
-/* Queues a query (never blocks, never launches).  *ticket identifies it. */
+/* Queues a query (never blocks, never launches).  *ticket identifies it.
+ * AGG_ERR_INVALID_ARG when its arrays are not device memory, its values are
+ * missing while SUM, MIN or MAX is asked for, its keys or values are not aligned
+ * to their element size, or its budget exceeds the pool; nothing is queued. */
 agg_status agg_server_submit(agg_server* s, const agg_query* q, uint64_t* ticket);
 
 /* One turn of the request loop: notices finished queries (freeing their budget

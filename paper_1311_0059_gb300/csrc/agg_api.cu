@@ -181,6 +181,31 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Checks the pointers of one group-by's input and output: device memory the
+// kernel can address (so that a misplaced host pointer is an argument error,
+// not a device fault), values present when an aggregate needs them, and keys
+// and values aligned to their element size.  d_n_groups is checked only where
+// the call uses it.
+agg_status check_device_io(uint32_t ops, int32_t value_type, const int64_t* d_keys, const void* d_vals, uint64_t n,
+                           const agg_output* out, bool uses_d_n_groups) {
+  const bool need_vals = (ops & ~(uint32_t)AGG_COUNT) != 0;
+  if (n > 0) {
+    if (!is_device_ptr(d_keys)) return AGG_ERR_INVALID_ARG;
+    if (need_vals && !is_device_ptr(d_vals)) return AGG_ERR_INVALID_ARG;
+    if (d_vals && !is_device_ptr(d_vals)) return AGG_ERR_INVALID_ARG;
+  }
+  if (!out->keys || !is_device_ptr(out->keys)) return AGG_ERR_INVALID_ARG;
+  if ((ops & AGG_COUNT) && !is_device_ptr(out->count)) return AGG_ERR_INVALID_ARG;
+  if ((ops & AGG_SUM) && !is_device_ptr(out->sum)) return AGG_ERR_INVALID_ARG;
+  if ((ops & AGG_MIN) && !is_device_ptr(out->min)) return AGG_ERR_INVALID_ARG;
+  if ((ops & AGG_MAX) && !is_device_ptr(out->max)) return AGG_ERR_INVALID_ARG;
+  if (uses_d_n_groups && out->d_n_groups && !is_device_ptr(out->d_n_groups)) return AGG_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_keys) & 7) ||
+      (d_vals && (reinterpret_cast<uintptr_t>(d_vals) & (value_type == AGG_I64 ? 7 : 3))))
+    return AGG_ERR_INVALID_ARG;
+  return AGG_OK;
+}
+
 void free_staging(agg_handle* h) {
   for (int a = 0; a < 2; ++a) {
     if (h->stg_mem[a]) cudaFree(h->stg_mem[a]);
@@ -402,21 +427,8 @@ agg_status agg_run(agg_handle* h, const int64_t* d_keys, const void* d_vals, uin
   if (!h || !out) return AGG_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bool need_vals = (h->spec.ops & ~(uint32_t)AGG_COUNT) != 0;
-  if (n > 0) {
-    if (!is_device_ptr(d_keys)) return AGG_ERR_INVALID_ARG;
-    if (need_vals && !is_device_ptr(d_vals)) return AGG_ERR_INVALID_ARG;
-    if (d_vals && !is_device_ptr(d_vals)) return AGG_ERR_INVALID_ARG;
-  }
-  if (!out->keys || !is_device_ptr(out->keys)) return AGG_ERR_INVALID_ARG;
-  if ((h->spec.ops & AGG_COUNT) && !is_device_ptr(out->count)) return AGG_ERR_INVALID_ARG;
-  if ((h->spec.ops & AGG_SUM) && !is_device_ptr(out->sum)) return AGG_ERR_INVALID_ARG;
-  if ((h->spec.ops & AGG_MIN) && !is_device_ptr(out->min)) return AGG_ERR_INVALID_ARG;
-  if ((h->spec.ops & AGG_MAX) && !is_device_ptr(out->max)) return AGG_ERR_INVALID_ARG;
-  if (out->d_n_groups && !is_device_ptr(out->d_n_groups)) return AGG_ERR_INVALID_ARG;
-  if ((reinterpret_cast<uintptr_t>(d_keys) & 7) ||
-      (d_vals && (reinterpret_cast<uintptr_t>(d_vals) & (h->spec.value_type == AGG_I64 ? 7 : 3))))
-    return AGG_ERR_INVALID_ARG;
+  const agg_status io = check_device_io(h->spec.ops, h->spec.value_type, d_keys, d_vals, n, out, true);
+  if (io != AGG_OK) return io;
 
   if (h->spec.path == AGG_PATH_SORT) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -817,8 +829,9 @@ agg_status agg_batch_create(const agg_spec* spec, const agg_batch_item* items, u
   };
   std::vector<Plan> plan(count);
   for (uint32_t i = 0; i < count; ++i) {
-    if (items[i].n > 0 && !is_device_ptr(items[i].d_keys)) return fail(AGG_ERR_INVALID_ARG);
-    if (!items[i].out.keys || !is_device_ptr(items[i].out.keys)) return fail(AGG_ERR_INVALID_ARG);
+    const agg_status io =
+        check_device_io(spec->ops, spec->value_type, items[i].d_keys, items[i].d_vals, items[i].n, &items[i].out, false);
+    if (io != AGG_OK) return fail(io);
     Layout L;
     if (!layout_for(items[i].budget, b->es, &L)) return fail(AGG_ERR_BUDGET_TOO_SMALL);
     agg_spec si = *spec;
@@ -1240,7 +1253,11 @@ agg_status agg_server_submit(agg_server* s, const agg_query* q, uint64_t* ticket
   Layout L;
   if (!layout_for(q->budget, s->es, &L)) return AGG_ERR_BUDGET_TOO_SMALL;
   if (L.total > s->pool_bytes) return AGG_ERR_INVALID_ARG;  // could never be admitted
-  if (!q->out.keys || (q->n > 0 && !q->d_keys)) return AGG_ERR_INVALID_ARG;
+  {
+    DeviceGuard g(s->device);
+    const agg_status io = check_device_io(s->spec.ops, s->spec.value_type, q->d_keys, q->d_vals, q->n, &q->out, false);
+    if (io != AGG_OK) return io;
+  }
   const uint64_t t = s->next_ticket++;
   ServerQuery& sq = s->queries[t];
   sq.q = *q;

@@ -71,3 +71,17 @@ def test_batch_workload_generator_is_deterministic():
                                                                       for w in b]
     ns = np.array([w.n for w in dg.batch_workloads(4096)])
     assert ns.min() >= 1000 and ns.max() <= 4_000_000
+
+
+def test_batch_rejects_pointers_the_kernel_cannot_use():
+    # an instance with host keys, host values or no values (SUM needs them)
+    # makes agg_batch_create fail with an argument error, before any launch
+    import torch
+    from paper_1311_0059_gb300 import AGG_I64, _abi
+    from paper_1311_0059_gb300.groupby import Batch
+    k = torch.arange(1000, dtype=torch.int64, device="cuda")
+    v = torch.ones(1000, dtype=torch.int64, device="cuda")
+    for bad in ((k.cpu(), v, 4 * MB, 0), (k, v.cpu(), 4 * MB, 0), (k, None, 4 * MB, 0)):
+        with pytest.raises(_abi.AggError) as e:
+            Batch([(k, v, 4 * MB, 0), bad], ops=15, value_type=AGG_I64)
+        assert e.value.status == _abi.AGG_ERR_INVALID_ARG

@@ -89,3 +89,37 @@ def test_served_rejects_budget_larger_than_pool():
     with pytest.raises(_abi.AggError):
         srv.submit(k, k, 64 * MB, Output(10, 15, "cuda"))
     srv.close()
+
+
+def test_served_rejects_pointers_the_kernel_cannot_use():
+    # host memory, missing values, misaligned keys: argument errors at submit,
+    # before anything is queued; a valid query on the same server still runs
+    import torch
+    from paper_1311_0059_gb300 import _abi
+    from paper_1311_0059_gb300.groupby import Output, Server
+    srv = Server(16 * MB, max_active=2)
+    k = torch.arange(1000, dtype=torch.int64, device="cuda")
+    v = torch.ones(1000, dtype=torch.int64, device="cuda")
+    raw = torch.zeros(1001, dtype=torch.int64, device="cuda")
+    out = Output(1000, 15, "cuda")
+
+    class _Shifted:  # device keys 4 bytes off their 8-byte alignment
+        def data_ptr(self):
+            return raw.data_ptr() + 4
+
+        def numel(self):
+            return 1000
+
+    for kk, vv, oo in ((k.cpu(), v, out), (k, None, out), (k, v.cpu(), out), (k, v, Output(1000, 15, "cpu")),
+                       (_Shifted(), v, out)):
+        with pytest.raises(_abi.AggError) as e:
+            srv.submit(kk, vv, 4 * MB, oo)
+        assert e.value.status == _abi.AGG_ERR_INVALID_ARG
+    assert srv.stats()["submitted"] == 0
+    t = srv.submit(k, v, 4 * MB, out)
+    deadline = time.perf_counter() + 60
+    while srv.stats()["completed"] < 1 and time.perf_counter() < deadline:
+        srv.progress()
+    info = srv.poll(t)
+    assert info.state == _abi.AGG_QUERY_DONE and info.status == 0 and info.n_groups == 1000
+    srv.close()
