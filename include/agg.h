@@ -92,6 +92,10 @@ typedef struct agg_tuning {
                               runs out ends the run with AGG_ERR_TIMEOUT (agg_sync) and the
                               handle is rebuilt */
   double fudge;            /* fudge factor F of Eq. 1 (default 1.2, Section 6.7) */
+  uint32_t in_budget;      /* in-budget paths for inputs whose every group fits the table at once
+                              (n at most half the slots): 0 = default (on), 2 = off (always the
+                              spilling path).  Results do not depend on it */
+  uint32_t reserved;       /* must be 0 */
 } agg_tuning;
 
 /* Output arrays, device pointers owned by the caller, one row per group.
@@ -142,6 +146,10 @@ typedef struct agg_plan_info {
   uint64_t active_slots;    /* slots used at level 0 for this n */
   uint64_t working_bytes;   /* bytes of the budget in use */
   uint64_t staging_bytes;   /* staging reserved for n rows */
+  uint64_t in_budget_path;  /* path agg_run takes for n rows: 0 = spilling hybrid hash, 1 = in-budget,
+                               partitioned into shared-memory tables (small n), 2 = in-budget, one
+                               table probed linearly (n at most half the slots) */
+  uint64_t partitions;      /* partitions of path 1 (else 0) */
 } agg_plan_info;
 
 typedef struct agg_handle agg_handle;
@@ -283,26 +291,45 @@ typedef struct agg_server_stats {
   uint64_t submitted, completed, running, queued;
   uint64_t pool_bytes, pool_in_use, pool_peak;  /* working memory of admitted queries */
   uint64_t max_concurrent;                      /* most queries running at once */
+  uint64_t staging_bytes, staging_in_use, staging_peak;  /* staging pool of queries that may spill */
+  uint64_t blocks, blocks_in_use;               /* co-resident thread blocks, and those held by running queries */
 } agg_server_stats;
+
+/* Smallest staging pool of a server (see agg_server_create). */
+#define AGG_SERVER_MIN_STAGING ((size_t)1 << 30)
 
 typedef struct agg_server agg_server;
 
 /* Creates a server with a device memory pool of pool_bytes for the working
  * memory of its queries (their declared budgets, the multi-user memory
  * constraint of Section 3.2) and at most max_active queries running at once.
+ * Beside it, in the same allocation, the server keeps a staging pool of
+ * max(pool_bytes / 2, AGG_SERVER_MIN_STAGING) bytes for the spill staging of
+ * the queries that may spill (outside their budgets, as the paper's M excludes
+ * disk).  Nothing else is allocated while queries run.
  * spec.ops and spec.value_type apply to every query. */
 agg_status agg_server_create(const agg_spec* spec, size_t pool_bytes, uint32_t max_active, agg_server** out);
 
 /* Queues a query (never blocks, never launches).  *ticket identifies it.
  * AGG_ERR_INVALID_ARG when its arrays are not device memory, its values are
  * missing while SUM, MIN or MAX is asked for, its keys or values are not aligned
- * to their element size, or its budget exceeds the pool; nothing is queued. */
+ * to their element size, its budget exceeds the pool, or its staging could not
+ * fit the staging pool; nothing is queued then. */
 agg_status agg_server_submit(agg_server* s, const agg_query* q, uint64_t* ticket);
 
-/* One turn of the request loop: notices finished queries (freeing their budget
- * and slot), then admits queued queries in arrival order while a slot is free
- * and the next query's budget fits the free pool, each launched at once on its
- * slot's stream so that admitted queries run concurrently.  Non-blocking.
+/* One turn of the request loop: notices finished queries (freeing their
+ * budget, staging, thread blocks and slot), then admits queued queries in
+ * arrival order, each launched at once on its slot's stream so that admitted
+ * queries run concurrently.  A query is admitted when a slot is free, its
+ * declared budget fits the free pool, its staging (if it may spill) fits the
+ * staging pool, and enough thread blocks are free: the teams of running queries
+ * never add up to more blocks than the GPU holds at once, so their cooperative
+ * grids never wait on one another.  A query wants about one block per 64k rows
+ * (a power of two, 8 to the whole GPU) and gets fewer when fewer are free (at
+ * least 8, or all it wants if less).  Queries wanting more than 32 blocks share
+ * all but a quarter of the blocks, which stays free for the small ones; such a
+ * query waiting for blocks does not hold back the smaller queries behind it,
+ * while one waiting for memory holds back every later query.  Non-blocking.
  * *completed (may be NULL) receives the number of queries finished now. */
 agg_status agg_server_progress(agg_server* s, uint32_t* completed);
 
@@ -326,16 +353,23 @@ agg_status agg_server_destroy(agg_server* s);
  * Nothing is allocated: the working memory (about 17 MB: control block, tag
  * bytes and AGG_NOALLOC_SLOTS table entries) is a file-scope __device__ array
  * of libagg.so that every GPU loading the library holds until the process
- * exits.  n may be at most AGG_NOALLOC_MAX_ROWS (else AGG_ERR_INVALID_ARG, and
- * nothing runs), which keeps every group resident with no staging area.
+ * exits.  n may be at most AGG_NOALLOC_MAX_ROWS, a quarter of the slots (else
+ * AGG_ERR_INVALID_ARG, and nothing runs).  The run uses the in-budget path of
+ * agg_run for small inputs: rows are split by hash into partitions that thread
+ * blocks aggregate in shared memory, and a key that does not fit there probes
+ * linearly across the table's slots, so every group is resident whatever the
+ * keys' hashes (key sets built to collide included), and no staging area is
+ * ever needed.
  * spec: as for agg_create, with path AGG_PATH_HASH.  d_keys, d_vals, out: as
  * for agg_run (device pointers, caller-owned).  The call enqueues the work on
- * `stream`, waits for it, and returns the run's status, with the group count in
- * *n_groups (may be NULL).  The first call on a device sets that device up (it
- * looks up the array's device address and the kernel's launch shape), so make
- * it before any stream capture.  Every call shares the one array and clears it
- * first: calls whose work overlaps on the GPU (other streams, other threads)
- * race on it and must be serialised by the caller. */
+ * `stream`, reads the status and group count back in stream order, waits for
+ * them, and returns the run's status (AGG_ERR_OUTPUT_CAPACITY when the groups
+ * exceed out->capacity), with the group count in *n_groups (may be NULL).  The
+ * first call on a device sets that device up (it looks up the array's device
+ * address and the kernels' launch shape), so make it before any stream
+ * capture.  Every call shares the one array and clears the part it uses first:
+ * calls whose work overlaps on the GPU (other streams, other threads) race on
+ * it and must be serialised by the caller. */
 agg_status agg_run_noalloc(const agg_spec* spec, const int64_t* d_keys, const void* d_vals, uint64_t n,
                            const agg_output* out, uint64_t* n_groups, void* stream);
 

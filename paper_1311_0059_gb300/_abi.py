@@ -42,7 +42,7 @@ class agg_spec(ctypes.Structure):
 class agg_tuning(ctypes.Structure):
     _fields_ = [("max_load_factor", ctypes.c_double), ("smem_entries", ctypes.c_uint32),
                 ("fan_out", ctypes.c_uint32), ("warp_dedup", ctypes.c_uint32), ("wait_limit_us", ctypes.c_uint32),
-                ("fudge", ctypes.c_double)]
+                ("fudge", ctypes.c_double), ("in_budget", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class agg_output(ctypes.Structure):
@@ -68,7 +68,8 @@ class agg_stats(ctypes.Structure):
 
 class agg_plan_info(ctypes.Structure):
     _fields_ = [("entry_bytes", _U64), ("table_slots", _U64), ("table_capacity", _U64), ("fan_out", _U64),
-                ("active_slots", _U64), ("working_bytes", _U64), ("staging_bytes", _U64)]
+                ("active_slots", _U64), ("working_bytes", _U64), ("staging_bytes", _U64),
+                ("in_budget_path", _U64), ("partitions", _U64)]
 
 
 class agg_batch_item(ctypes.Structure):
@@ -94,7 +95,9 @@ class agg_query_info(ctypes.Structure):
 
 class agg_server_stats(ctypes.Structure):
     _fields_ = [("submitted", _U64), ("completed", _U64), ("running", _U64), ("queued", _U64),
-                ("pool_bytes", _U64), ("pool_in_use", _U64), ("pool_peak", _U64), ("max_concurrent", _U64)]
+                ("pool_bytes", _U64), ("pool_in_use", _U64), ("pool_peak", _U64), ("max_concurrent", _U64),
+                ("staging_bytes", _U64), ("staging_in_use", _U64), ("staging_peak", _U64), ("blocks", _U64),
+                ("blocks_in_use", _U64)]
 
 
 AGG_QUERY_QUEUED, AGG_QUERY_RUNNING, AGG_QUERY_DONE, AGG_QUERY_FAILED = 0, 1, 2, 3

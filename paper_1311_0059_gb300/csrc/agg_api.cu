@@ -53,6 +53,9 @@ struct agg_handle {
   cudaStream_t last_stream = nullptr;
   bool ran = false;
   uint64_t launches = 0;
+  // entries [dirty_lo, slots) hold scratch records of the partitioned in-budget
+  // path (slots = none); they are restored before another run needs them
+  uint64_t dirty_lo = 0;
 };
 
 namespace {
@@ -99,6 +102,7 @@ agg_tuning effective(const agg_tuning* t) {
   e.warp_dedup = (t && t->warp_dedup) ? t->warp_dedup : 2;  // off unless asked for
   e.fudge = (t && t->fudge > 0) ? t->fudge : DEFAULT_FUDGE;
   e.wait_limit_us = t ? t->wait_limit_us : 0;
+  e.in_budget = (t && t->in_budget) ? t->in_budget : 1;  // on unless asked off
   return e;
 }
 
@@ -112,6 +116,7 @@ bool valid_tuning(const agg_tuning* t) {
   if (t->warp_dedup > 2) return false;
   if (t->wait_limit_us > MAX_WAIT_LIMIT_US) return false;
   if (t->fudge < 0 || t->fudge > 16) return false;
+  if (t->in_budget > 2 || t->reserved != 0) return false;
   return true;
 }
 
@@ -256,6 +261,7 @@ agg_status reinit_working(agg_handle* h, cudaStream_t s) {
     return AGG_ERR_CUDA;
   if (hash_init_table(h->ent, h->tags, (uint32_t)h->slots, h->ent_kind, s) != cudaSuccess) return AGG_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return AGG_ERR_CUDA;
+  h->dirty_lo = h->slots;
   return AGG_OK;
 }
 
@@ -305,6 +311,20 @@ agg_status agg_plan(size_t budget, const agg_spec* spec, const agg_tuning* t, ui
   out->working_bytes = L.total;
   const uint64_t chunks = (n + CH - 1) / CH + 152ull * 2 * out->fan_out + 8;
   out->staging_bytes = 2 * (chunks * CH * REC_BYTES + 3 * chunks * 4);
+  out->in_budget_path = 0;
+  out->partitions = 0;
+  if (spec->path == AGG_PATH_HASH && e.in_budget != 2) {
+    PartPlan pp;
+    if (e.smem_entries != 1 && hash_part_plan(n, L.slots, es, e.smem_entries > 1 ? e.smem_entries : DEFAULT_NS, &pp)) {
+      out->in_budget_path = 1;
+      out->partitions = 1ull << pp.plog;
+      out->active_slots = pp.s_ovf;
+    } else if (const uint32_t sf = hash_fast_slots(n, L.slots)) {
+      out->in_budget_path = 2;
+      out->active_slots = sf;
+    }
+    if (out->in_budget_path) out->staging_bytes = 0;
+  }
   return AGG_OK;
 }
 
@@ -455,7 +475,12 @@ namespace {
 agg_status hash_enqueue(agg_handle* h, const int64_t* d_keys, const void* d_vals, uint64_t n, const agg_output* out,
                         cudaStream_t s, bool host_input) {
   const uint32_t fan = plan_fan(&h->spec, h->tune, n, h->budget, h->es);
-  if (!h->stg_mem[0] || n > h->reserved_rows || fan > h->reserved_fan) {
+  const uint32_t ns = h->tune.smem_entries > 1 ? h->tune.smem_entries : DEFAULT_NS;
+  PartPlan pp;
+  const bool in_budget = h->tune.in_budget != 2;
+  const bool part = in_budget && h->tune.smem_entries != 1 && hash_part_plan(n, h->slots, h->es, ns, &pp);
+  const uint32_t s_fast = part || !in_budget ? 0u : hash_fast_slots(n, h->slots);
+  if (!part && !s_fast && (!h->stg_mem[0] || n > h->reserved_rows || fan > h->reserved_fan)) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
       return AGG_ERR_INVALID_ARG;  // staging must be reserved before capture
@@ -499,6 +524,41 @@ agg_status hash_enqueue(agg_handle* h, const int64_t* d_keys, const void* d_vals
   p.dedup = h->tune.warp_dedup == 1 ? 1 : 0;
   p.no_prefetch = host_input ? 1 : 0;
   p.timeout_ns = h->tune.wait_limit_us ? 1000ull * h->tune.wait_limit_us : TIMEOUT_NS;
+  // entries this run needs clear: the overflow table, the fast table, or all
+  const uint64_t need_clear = part ? pp.s_ovf + 1ull : s_fast ? (uint64_t)s_fast : h->slots;
+  if (h->dirty_lo < h->slots && need_clear > h->dirty_lo) {
+    if (hash_reset_entries(h->ent + h->dirty_lo * h->es, h->slots - h->dirty_lo, h->ent_kind, s) != cudaSuccess) {
+      cudaGetLastError();
+      return AGG_ERR_CUDA;
+    }
+    h->launches += 1;
+    h->dirty_lo = h->slots;
+  }
+  if (part) {
+    // a small input: partitioned into shared-memory tables, no global atomics
+    p.s_act0 = pp.s_ovf;
+    if (hash_part_launch(h->ent_kind, h->spec.value_type, p, pp, h->es, h->ki.smem, s) != cudaSuccess) {
+      cudaGetLastError();
+      return AGG_ERR_CUDA;
+    }
+    h->dirty_lo = std::min<uint64_t>(h->dirty_lo, pp.scratch_slot);
+    h->launches += 2;
+    h->last_stream = s;
+    h->ran = true;
+    return AGG_OK;
+  }
+  if (s_fast) {
+    // every distinct key fits: one pass in place, no spill, no grid barrier
+    p.s_act0 = s_fast;
+    if (hash_fast_launch(h->ent_kind, h->spec.value_type, p, s_fast, h->ki.smem, s) != cudaSuccess) {
+      cudaGetLastError();
+      return AGG_ERR_CUDA;
+    }
+    h->launches += n > 0 ? 2 : 1;
+    h->last_stream = s;
+    h->ran = true;
+    return AGG_OK;
+  }
   if (hash_launch(h->ent_kind, h->spec.value_type, p, h->ki, s) != cudaSuccess) {
     cudaGetLastError();
     return AGG_ERR_CUDA;
@@ -1040,8 +1100,17 @@ agg_status agg_batch_destroy(agg_batch* b) {
 struct ServerQuery {
   agg_query q{};
   agg_query_info info{};
-  uint64_t pool_off = 0, pool_len = 0;
+  uint64_t pool_off = 0, pool_len = 0;  // working memory (declared budget) in the pool
+  uint64_t stg_off = 0, stg_len = 0;    // staging in the staging pool (0 when the query cannot spill)
+  uint32_t team = 0;                    // thread blocks it holds while it runs
   int slot = -1;
+};
+
+// One pool of device memory carved into ranges (first fit, neighbours merged).
+struct RangePool {
+  uint8_t* base = nullptr;
+  uint64_t bytes = 0, in_use = 0, peak = 0;
+  std::map<uint64_t, uint64_t> free_list;  // offset -> length
 };
 
 struct agg_server {
@@ -1051,9 +1120,12 @@ struct agg_server {
   uint32_t es = 32;
   agg_tuning tune{};
   KernelInfo ki{};  // launch shape of one block team (smem) and the whole-GPU block count
-  uint8_t* pool = nullptr;
-  uint64_t pool_bytes = 0, in_use = 0, peak = 0;
-  std::map<uint64_t, uint64_t> free_list;  // offset -> length
+  void* mem = nullptr;  // one allocation: the working-memory pool, then the staging pool
+  RangePool pool;       // declared budgets of admitted queries (Section 3.2)
+  RangePool stage;      // their staging areas (outside the budgets, like the paper's disk)
+  uint32_t blocks_in_use = 0, big_blocks_in_use = 0;
+  uint32_t inject_fail_at = 0;  // test hook: the k-th launch (1-based) fails after its set-up was queued
+  uint32_t launches = 0;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
   std::vector<int64_t> slot_ticket;  // -1 = free
@@ -1070,87 +1142,116 @@ struct agg_server {
 
 namespace {
 
-bool pool_alloc(agg_server* s, uint64_t len, uint64_t* off) {
+bool pool_alloc(RangePool& p, uint64_t len, uint64_t* off) {
   len = align_up(len, 256);
-  for (auto it = s->free_list.begin(); it != s->free_list.end(); ++it) {
+  if (len == 0) {
+    *off = 0;
+    return true;
+  }
+  for (auto it = p.free_list.begin(); it != p.free_list.end(); ++it) {
     if (it->second < len) continue;
     *off = it->first;
     const uint64_t rest = it->second - len, roff = it->first + len;
-    s->free_list.erase(it);
-    if (rest) s->free_list[roff] = rest;
-    s->in_use += len;
-    s->peak = std::max(s->peak, s->in_use);
+    p.free_list.erase(it);
+    if (rest) p.free_list[roff] = rest;
+    p.in_use += len;
+    p.peak = std::max(p.peak, p.in_use);
     return true;
   }
   return false;
 }
 
-void pool_free(agg_server* s, uint64_t off, uint64_t len) {
+void pool_free(RangePool& p, uint64_t off, uint64_t len) {
   len = align_up(len, 256);
-  s->in_use -= len;
-  auto it = s->free_list.emplace(off, len).first;
+  if (len == 0) return;
+  p.in_use -= len;
+  auto it = p.free_list.emplace(off, len).first;
   auto nx = std::next(it);
-  if (nx != s->free_list.end() && it->first + it->second == nx->first) {  // merge with the next
+  if (nx != p.free_list.end() && it->first + it->second == nx->first) {  // merge with the next
     it->second += nx->second;
-    s->free_list.erase(nx);
+    p.free_list.erase(nx);
   }
-  if (it != s->free_list.begin()) {  // merge with the previous
+  if (it != p.free_list.begin()) {  // merge with the previous
     auto pv = std::prev(it);
     if (pv->first + pv->second == it->first) {
       pv->second += it->second;
-      s->free_list.erase(it);
+      p.free_list.erase(it);
     }
   }
 }
 
-// Thread blocks of a query's team: more rows, more blocks (power of two, at
-// most half the GPU so that other queries keep running beside it).  A server
-// that runs one query at a time gives each query the whole GPU.
-uint32_t team_for(uint64_t n, uint32_t all_blocks, uint32_t max_active) {
+// Thread blocks a query would like: about 64k rows per block, a power of two
+// from 8 to the whole GPU.  A server that runs one query at a time gives each
+// query the whole GPU.
+uint32_t team_wanted(uint64_t n, uint32_t all_blocks, uint32_t max_active) {
   if (max_active == 1) return all_blocks;
   uint32_t b = 8;
-  while (b < all_blocks / 2 && (uint64_t)b * (1ull << 18) < n) b <<= 1;
-  return std::min(b, std::max(1u, all_blocks / 2));
+  while (b < all_blocks && (uint64_t)b * 65536 < n) b <<= 1;
+  return std::min(b, all_blocks);
 }
 
-agg_status server_launch(agg_server* s, ServerQuery& sq, int slot) {
-  cudaStream_t st = s->streams[slot];
-  const agg_query& q = sq.q;
+// Queries that want more than SMALL_TEAM blocks are "big"; together they may
+// hold at most all_blocks - all_blocks / SMALL_RESERVE_DIV blocks, so that
+// the small queries (most arrivals) always find blocks free at once instead of
+// waiting behind a long query.
+constexpr uint32_t SMALL_TEAM = 32;
+constexpr uint32_t SMALL_RESERVE_DIV = 4;
+
+struct QueryPlan {
   Layout L;
-  layout_for(q.budget, s->es, &L);
-  uint8_t* base = s->pool + sq.pool_off;
-  Ctrl* ctrl = reinterpret_cast<Ctrl*>(base);
-  uint32_t* tags = reinterpret_cast<uint32_t*>(base + L.tags_off);
-  uint8_t* ent = base + L.ent_off;
+  uint64_t slots = 0, chunks = 0, data = 0, meta = 0, stg_len = 0;
+  uint32_t fan = 16, team = 0;
+  bool may_spill = false;
+};
+
+// Table size, fan-out and staging of a query run by `team` blocks.
+QueryPlan plan_query(const agg_server* s, const agg_query& q, uint32_t team) {
+  QueryPlan P;
+  layout_for(q.budget, s->es, &P.L);
   const uint64_t n = q.n;
   uint64_t need = (uint64_t)((double)(n ? n : 1) / s->tune.max_load_factor) + BUCKET;
   need = std::max<uint64_t>((need + BUCKET - 1) / BUCKET * BUCKET, 2 * MIN_SLOTS);
-  const uint64_t slots = std::min<uint64_t>(L.slots, need);
-  const bool may_spill = n > (uint64_t)(0.5 * (double)slots);
+  P.slots = std::min<uint64_t>(P.L.slots, need);
+  P.may_spill = n > (uint64_t)(0.5 * (double)P.slots);
   agg_spec si = s->spec;
   si.expected_groups = q.expected_groups;
-  const uint32_t fan = plan_fan(&si, s->tune, n, q.budget, s->es);
-  const uint32_t team = team_for(n, (uint32_t)s->ki.blocks, (uint32_t)s->slot_ticket.size());
+  P.fan = plan_fan(&si, s->tune, n, q.budget, s->es);
+  P.team = team;
+  if (P.may_spill) {
+    P.chunks = (n + CH - 1) / CH + (uint64_t)team * P.fan + 8;
+    P.data = align_up(P.chunks * CH * REC_BYTES, 256);
+    P.meta = align_up(P.chunks * 4, 256);
+    P.stg_len = 2 * (P.data + 3 * P.meta);
+  }
+  return P;
+}
+
+// Enqueues the set-up and the kernel of an admitted query on its slot's stream.
+// On an error the caller must let the slot's stream drain before it frees the
+// query's pool ranges (work queued before the error may still use them).
+agg_status server_launch(agg_server* s, ServerQuery& sq, const QueryPlan& P, int slot) {
+  cudaStream_t st = s->streams[slot];
+  const agg_query& q = sq.q;
+  uint8_t* base = s->pool.base + sq.pool_off;
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(base);
+  uint32_t* tags = reinterpret_cast<uint32_t*>(base + P.L.tags_off);
+  uint8_t* ent = base + P.L.ent_off;
+  const uint64_t n = q.n;
   if (q.ready && cudaStreamWaitEvent(st, static_cast<cudaEvent_t>(q.ready), 0) != cudaSuccess) return AGG_ERR_CUDA;
   if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st) != cudaSuccess ||
-      hash_init_table(ent, tags, (uint32_t)slots, s->ent_kind, st) != cudaSuccess)
+      hash_init_table(ent, tags, (uint32_t)P.slots, s->ent_kind, st) != cudaSuccess)
     return AGG_ERR_CUDA;
+  s->launches += 1;
+  if (s->inject_fail_at && s->launches == s->inject_fail_at) return AGG_ERR_CUDA;  // host-injected failure
   HashParams p{};
-  void* stg = nullptr;
-  uint64_t chunks = 0, data = 0, meta = 0;
-  if (may_spill) {
-    chunks = (n + CH - 1) / CH + (uint64_t)team * fan + 8;
-    data = align_up(chunks * CH * REC_BYTES, 256);
-    meta = align_up(chunks * 4, 256);
-    if (cudaMallocAsync(&stg, 2 * (data + 3 * meta), st) != cudaSuccess) return AGG_ERR_OOM;
-  }
+  uint8_t* stg = P.stg_len ? s->stage.base + sq.stg_off : nullptr;
   for (int a = 0; a < 2; ++a) {
-    uint8_t* area = stg ? static_cast<uint8_t*>(stg) + a * (data + 3 * meta) : nullptr;
+    uint8_t* area = stg ? stg + a * (P.data + 3 * P.meta) : nullptr;
     p.stg[a] = area;
-    p.dir_part[a] = area ? reinterpret_cast<uint32_t*>(area + data) : nullptr;
-    p.dir_count[a] = area ? reinterpret_cast<uint32_t*>(area + data + meta) : nullptr;
-    p.list[a] = area ? reinterpret_cast<uint32_t*>(area + data + 2 * meta) : nullptr;
-    p.max_chunks[a] = area ? chunks : 0;
+    p.dir_part[a] = area ? reinterpret_cast<uint32_t*>(area + P.data) : nullptr;
+    p.dir_count[a] = area ? reinterpret_cast<uint32_t*>(area + P.data + P.meta) : nullptr;
+    p.list[a] = area ? reinterpret_cast<uint32_t*>(area + P.data + 2 * P.meta) : nullptr;
+    p.max_chunks[a] = area ? P.chunks : 0;
   }
   p.keys = q.d_keys;
   p.vals = q.d_vals;
@@ -1168,26 +1269,34 @@ agg_status server_launch(agg_server* s, ServerQuery& sq, int slot) {
   p.ctrl = ctrl;
   p.ent = ent;
   p.tags = tags;
-  p.slots = (uint32_t)slots;
+  p.slots = (uint32_t)P.slots;
   p.seed = s->spec.seed;
   p.ops = s->spec.ops;
-  p.fan_log2 = log2u(fan);
+  p.fan_log2 = log2u(P.fan);
   p.lf = s->tune.max_load_factor;
-  p.s_act0 = active_slots(q.expected_groups ? q.expected_groups : (n ? n : 1), p.lf, slots);
+  p.s_act0 = active_slots(q.expected_groups ? q.expected_groups : (n ? n : 1), p.lf, P.slots);
   p.ns = s->tune.smem_entries;
   p.cache = 1;
   p.dedup = s->tune.warp_dedup == 1 ? 1 : 0;
   p.timeout_ns = TIMEOUT_NS;
   KernelInfo ki = s->ki;
-  ki.blocks = (int)team;
+  ki.blocks = (int)P.team;
   if (hash_launch(s->ent_kind, s->spec.value_type, p, ki, st) != cudaSuccess) return AGG_ERR_CUDA;
-  if (stg && cudaFreeAsync(stg, st) != cudaSuccess) return AGG_ERR_CUDA;
   if (cudaMemcpyAsync(s->pinned + 2 * slot, &ctrl->status_bits, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaMemcpyAsync(s->pinned + 2 * slot + 1, &ctrl->last_n_groups, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaEventRecord(s->events[slot], st) != cudaSuccess)
     return AGG_ERR_CUDA;
-  sq.info.team_blocks = team;
+  sq.info.team_blocks = P.team;
   return AGG_OK;
+}
+
+void release_query(agg_server* s, ServerQuery& sq) {
+  pool_free(s->pool, sq.pool_off, sq.pool_len);
+  pool_free(s->stage, sq.stg_off, sq.stg_len);
+  sq.pool_len = sq.stg_len = 0;
+  s->blocks_in_use -= sq.team;
+  if (sq.team > SMALL_TEAM) s->big_blocks_in_use -= sq.team;
+  sq.team = 0;
 }
 
 }  // namespace
@@ -1214,27 +1323,27 @@ agg_status agg_server_create(const agg_spec* spec, size_t pool_bytes, uint32_t m
   s->ent_kind = pick_ent(spec);
   s->es = entry_bytes(s->ent_kind);
   s->tune = effective(nullptr);
+  if (const char* e = std::getenv("AGG_INJECT_LAUNCH_FAILURE")) s->inject_fail_at = (uint32_t)std::strtoul(e, nullptr, 10);
   if (hash_kernel_info(s->ent_kind, spec->value_type, s->tune.smem_entries, s->device, &s->ki) != cudaSuccess) {
     cudaGetLastError();
     return fail(AGG_ERR_CUDA);
   }
-  if (cudaMalloc(reinterpret_cast<void**>(&s->pool), pool_bytes) != cudaSuccess) {
+  const uint64_t pool = align_up(pool_bytes, 256);
+  const uint64_t stage = align_up(std::max<uint64_t>(pool_bytes / 2, AGG_SERVER_MIN_STAGING), 256);
+  if (cudaMalloc(&s->mem, pool + stage) != cudaSuccess) {
     cudaGetLastError();
     return fail(AGG_ERR_OOM);
   }
-  s->pool_bytes = pool_bytes;
-  s->free_list[0] = pool_bytes;
+  s->pool.base = static_cast<uint8_t*>(s->mem);
+  s->pool.bytes = pool_bytes;
+  s->pool.free_list[0] = pool_bytes;
+  s->stage.base = static_cast<uint8_t*>(s->mem) + pool;
+  s->stage.bytes = stage;
+  s->stage.free_list[0] = stage;
   if (cudaMallocHost(reinterpret_cast<void**>(&s->pinned), 16ull * max_active) != cudaSuccess) {
     cudaGetLastError();
     return fail(AGG_ERR_OOM);
   }
-  // keep memory freed by cudaFreeAsync cached in the pool for the next query
-  cudaMemPool_t mp;
-  if (cudaDeviceGetDefaultMemPool(&mp, s->device) == cudaSuccess) {
-    uint64_t thr = ~0ull;
-    cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr);
-  }
-  cudaGetLastError();
   s->streams.resize(max_active, nullptr);
   s->events.resize(max_active, nullptr);
   s->slot_ticket.assign(max_active, -1);
@@ -1252,7 +1361,10 @@ agg_status agg_server_submit(agg_server* s, const agg_query* q, uint64_t* ticket
   if (!s || !q || !ticket) return AGG_ERR_INVALID_ARG;
   Layout L;
   if (!layout_for(q->budget, s->es, &L)) return AGG_ERR_BUDGET_TOO_SMALL;
-  if (L.total > s->pool_bytes) return AGG_ERR_INVALID_ARG;  // could never be admitted
+  if (L.total > s->pool.bytes) return AGG_ERR_INVALID_ARG;  // could never be admitted
+  // staging with the smallest team it may get must fit the staging pool
+  const uint32_t min_team = std::min<uint32_t>(8, (uint32_t)s->ki.blocks);
+  if (plan_query(s, *q, min_team).stg_len > s->stage.bytes) return AGG_ERR_INVALID_ARG;
   {
     DeviceGuard g(s->device);
     const agg_status io = check_device_io(s->spec.ops, s->spec.value_type, q->d_keys, q->d_vals, q->n, &q->out, false);
@@ -1289,14 +1401,27 @@ agg_status agg_server_progress(agg_server* s, uint32_t* completed) {
       sq.info.state = sq.info.status == AGG_OK ? AGG_QUERY_DONE : AGG_QUERY_FAILED;
       sq.info.n_groups = s->pinned[2 * slot + 1];
     }
-    pool_free(s, sq.pool_off, sq.pool_len);
+    release_query(s, sq);
     s->slot_ticket[slot] = -1;
     s->running -= 1;
     s->completed += 1;
     ++done;
   }
-  // admission in arrival order: a free slot and room for the declared budget
-  while (!s->waiting.empty()) {
+  // Admission in arrival order.  A query needs a free slot, room in the pool
+  // for its declared budget, room in the staging pool when it may spill, and
+  // thread blocks: the teams of running queries never add up to more blocks
+  // than the GPU holds at once, so that their cooperative grids never wait on
+  // one another.  A query gets the blocks it wants, or fewer (at least
+  // min(8, wanted)) when fewer are free.  Big queries (more than SMALL_TEAM
+  // blocks wanted) share all but a reserve of the blocks and are admitted in
+  // arrival order among themselves; a big query that must wait for blocks does
+  // not hold back the small queries behind it.  A query that must wait for
+  // memory holds back everything behind it, so that a large budget is never
+  // starved.
+  const uint32_t all = (uint32_t)s->ki.blocks;
+  const uint32_t big_cap = s->slot_ticket.size() == 1 ? all : all - all / SMALL_RESERVE_DIV;
+  bool big_blocked = false;
+  for (auto it = s->waiting.begin(); it != s->waiting.end();) {
     int slot = -1;
     for (size_t i = 0; i < s->slot_ticket.size(); ++i)
       if (s->slot_ticket[i] < 0) {
@@ -1304,24 +1429,45 @@ agg_status agg_server_progress(agg_server* s, uint32_t* completed) {
         break;
       }
     if (slot < 0) break;
-    const uint64_t t = s->waiting.front();
+    const uint64_t t = *it;
     ServerQuery& sq = s->queries[t];
-    Layout L;
-    layout_for(sq.q.budget, s->es, &L);
-    uint64_t off = 0;
-    if (!pool_alloc(s, L.total, &off)) break;
-    s->waiting.pop_front();
+    const uint32_t want = team_wanted(sq.q.n, all, (uint32_t)s->slot_ticket.size());
+    const bool big = want > SMALL_TEAM && s->slot_ticket.size() > 1;
+    uint32_t avail = all - s->blocks_in_use;
+    if (big) avail = std::min(avail, big_cap - std::min(big_cap, s->big_blocks_in_use));
+    const uint32_t team = std::min(want, avail);
+    if ((big && big_blocked) || team < std::min(want, 8u)) {
+      if (big) big_blocked = true;
+      ++it;
+      continue;
+    }
+    const QueryPlan P = plan_query(s, sq.q, team);
+    uint64_t off = 0, soff = 0;
+    if (!pool_alloc(s->pool, P.L.total, &off)) break;
+    if (!pool_alloc(s->stage, P.stg_len, &soff)) {
+      pool_free(s->pool, off, P.L.total);
+      break;
+    }
+    it = s->waiting.erase(it);
     sq.pool_off = off;
-    sq.pool_len = L.total;
+    sq.pool_len = P.L.total;
+    sq.stg_off = soff;
+    sq.stg_len = P.stg_len;
+    sq.team = team;
+    s->blocks_in_use += team;
+    if (team > SMALL_TEAM) s->big_blocks_in_use += team;
     sq.slot = slot;
-    const agg_status st = server_launch(s, sq, slot);
+    const agg_status st = server_launch(s, sq, P, slot);
     sq.info.t_start = s->now();
     if (st != AGG_OK) {
       cudaGetLastError();
-      pool_free(s, off, L.total);
+      // work queued before the failure may still use the ranges: let it drain
+      cudaStreamSynchronize(s->streams[slot]);
+      cudaGetLastError();
+      release_query(s, sq);
       sq.info.state = AGG_QUERY_FAILED;
       sq.info.status = st;
-      sq.info.t_done = sq.info.t_start;
+      sq.info.t_done = s->now();
       s->completed += 1;
       continue;
     }
@@ -1348,10 +1494,15 @@ agg_status agg_server_get_stats(agg_server* s, agg_server_stats* st) {
   st->completed = s->completed;
   st->running = s->running;
   st->queued = s->waiting.size();
-  st->pool_bytes = s->pool_bytes;
-  st->pool_in_use = s->in_use;
-  st->pool_peak = s->peak;
+  st->pool_bytes = s->pool.bytes;
+  st->pool_in_use = s->pool.in_use;
+  st->pool_peak = s->pool.peak;
   st->max_concurrent = s->max_conc;
+  st->staging_bytes = s->stage.bytes;
+  st->staging_in_use = s->stage.in_use;
+  st->staging_peak = s->stage.peak;
+  st->blocks = (uint64_t)s->ki.blocks;
+  st->blocks_in_use = s->blocks_in_use;
   return AGG_OK;
 }
 
@@ -1365,7 +1516,7 @@ agg_status agg_server_destroy(agg_server* s) {
     if (e) cudaEventDestroy(e);
   for (cudaStream_t st : s->streams)
     if (st) cudaStreamDestroy(st);
-  if (s->pool) cudaFree(s->pool);
+  if (s->mem) cudaFree(s->mem);
   if (s->pinned) cudaFreeHost(s->pinned);
   delete s;
   return AGG_OK;

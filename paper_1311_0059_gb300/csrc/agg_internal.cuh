@@ -128,6 +128,26 @@ struct KernelInfo {
 cudaError_t hash_kernel_info(int ent_kind, int vt, uint32_t ns, int device, KernelInfo* out);
 cudaError_t hash_launch(int ent_kind, int vt, const HashParams& p, const KernelInfo& ki, cudaStream_t s);
 cudaError_t hash_init_table(uint8_t* ent, uint32_t* tags, uint32_t slots, int ent_kind, cudaStream_t s);
+// In-budget fast path: the active slots for n rows, or 0 when n rows may not fit
+// (more than half the slots); then two ordinary launches (aggregate, emit).
+uint32_t hash_fast_slots(uint64_t n, uint64_t slots);
+cudaError_t hash_fast_launch(int ent_kind, int vt, const HashParams& p, uint32_t s_act, size_t smem, cudaStream_t s);
+// Partitioned in-budget path for small inputs (no global atomics): the plan
+// (false when n rows are too many, or the scratch and overflow table do not fit
+// the slots), then two launches (partition, aggregate + emit).  The scratch
+// occupies the entries from scratch_slot up to the side slot, which are left
+// dirty: the caller restores them before another path uses the table.
+struct PartPlan {
+  uint32_t nblk = 0;          // first-launch blocks (FAST rows each)
+  uint32_t plog = 0;          // log2 of the partitions
+  uint32_t s_ovf = 0;         // slots of the overflow table [0, s_ovf)
+  uint32_t scratch_slot = 0;  // first entry used as scratch
+};
+// Resets `count` table entries starting at ent to the empty state (tags untouched).
+cudaError_t hash_reset_entries(uint8_t* ent, uint64_t count, int ent_kind, cudaStream_t s);
+bool hash_part_plan(uint64_t n, uint64_t slots, uint32_t es, uint32_t ns, PartPlan* out);
+cudaError_t hash_part_launch(int ent_kind, int vt, const HashParams& p, const PartPlan& pp, uint32_t es, size_t smem,
+                             cudaStream_t s);
 cudaError_t hash_batch_kernel_info(int ent_kind, int vt, uint32_t ns, int device, KernelInfo* out);
 cudaError_t hash_batch_launch(int ent_kind, int vt, const HashParams* items, const uint32_t* team_off,
                               const uint32_t* team_items, uint32_t team_blocks, uint32_t nteams, size_t smem,

@@ -1643,6 +1643,542 @@ __global__ void __launch_bounds__(THREADS, 2)
   }
 }
 
+// ---------------------------------------------------------------- in-budget fast path
+
+// When a run has at most half as many rows as the table has slots, every
+// distinct key fits in the table at once, and the whole group-by completes in
+// place: a table that never fills needs no partitioning (Section 4.3.4).  Keys
+// then probe linearly across all active slots instead of only their bucket, so
+// no key is ever refused and nothing spills.  With no spill there is no phase to
+// wait for: the aggregation runs as one ordinary launch with no grid barrier,
+// and the emit as a second ordinary launch behind it in the stream.  Hot keys
+// are absorbed by the per-block shared-memory cache as at level 0.
+
+constexpr int FAST_RPT = 8;                              // rows per thread of the aggregation pass
+constexpr uint32_t FAST_ROWS = (uint32_t)THREADS * FAST_RPT;  // rows per block
+constexpr int EMIT_THREADS = 256;
+constexpr uint32_t EMIT_SLOTS = (uint32_t)EMIT_THREADS * 16;  // slots per emit block (16 tag bytes a thread)
+
+// Home slot of a key among s_act slots (hash bits 32..63).
+__device__ __forceinline__ uint32_t fast_home(uint64_t h, uint32_t s_act) {
+  return (uint32_t)(((h >> 32) * (uint64_t)s_act) >> 32);
+}
+
+// Finds or claims the slot of `key` by linear probing from `slot` (its home),
+// given the key word already loaded there (`k2`).  The table holds fewer
+// distinct keys than s_act, so a probe always ends.  A claimed slot gets its
+// tag byte, which marks it for the emit.
+template <int ENT>
+__device__ __forceinline__ uint32_t fast_probe(const HashParams& P, uint32_t s_act, long long key, uint64_t h,
+                                               uint32_t slot, long long k2) {
+  if (key == EMPTY_KEY) {  // the empty marker value itself: side slot
+    uint8_t* tb = reinterpret_cast<uint8_t*>(P.tags) + P.slots;
+    if (__ldcg(tb) == 0) __stcg(tb, (uint8_t)0x80);
+    return P.slots;
+  }
+  for (;;) {
+    if (k2 == key) return slot;
+    if (k2 == EMPTY_KEY) {
+      long long* kp = reinterpret_cast<long long*>(Ent<ENT>::at(P.ent, slot));
+      const long long old = (long long)atomicCAS(reinterpret_cast<unsigned long long*>(kp),
+                                                 (unsigned long long)EMPTY_KEY, (unsigned long long)key);
+      if (old == EMPTY_KEY) {
+        __stcg(reinterpret_cast<uint8_t*>(P.tags) + slot, (uint8_t)key_tag(h));
+        return slot;
+      }
+      if (old == key) return slot;
+    }
+    slot = slot + 1 == s_act ? 0u : slot + 1;
+    k2 = __ldcg(reinterpret_cast<const long long*>(Ent<ENT>::at(P.ent, slot)));
+  }
+}
+
+template <int ENT, int VT>
+__global__ void __launch_bounds__(THREADS, 2) fast_agg_kernel(const HashParams P, uint32_t s_act) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  const Cache cc = carve_cache(smem_raw + ((sizeof(Smem) + 15) & ~size_t(15)), P.cache ? P.ns : 0u, Ent<ENT>::MM);
+  const uint64_t seed0 = level_seed(P.seed, 0);
+  const uint64_t row0 = (uint64_t)blockIdx.x * FAST_ROWS;
+  long long k[FAST_RPT], v[FAST_RPT];
+  bool valid[FAST_RPT];
+  // every load of the block's rows first
+#pragma unroll
+  for (int j = 0; j < FAST_RPT / 2; ++j) {
+    const uint64_t row = row0 + (uint64_t)j * 2 * THREADS + 2 * threadIdx.x;
+    if (P.vec_ok && row + 1 < P.n) {
+      const longlong2 kk = __ldcs(reinterpret_cast<const longlong2*>(P.keys + row));
+      k[2 * j] = kk.x;
+      k[2 * j + 1] = kk.y;
+      if (!P.has_vals) {
+        v[2 * j] = v[2 * j + 1] = 0;
+      } else if (VT == AGG_I64) {
+        const longlong2 vv = __ldcs(reinterpret_cast<const longlong2*>(static_cast<const long long*>(P.vals) + row));
+        v[2 * j] = vv.x;
+        v[2 * j + 1] = vv.y;
+      } else {
+        const int2 vv = __ldcs(reinterpret_cast<const int2*>(static_cast<const int*>(P.vals) + row));
+        v[2 * j] = vv.x;
+        v[2 * j + 1] = vv.y;
+      }
+      valid[2 * j] = valid[2 * j + 1] = true;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const uint64_t rr = row + e;
+        valid[2 * j + e] = rr < P.n;
+        k[2 * j + e] = 0;
+        v[2 * j + e] = 0;
+        if (rr < P.n) {
+          k[2 * j + e] = __ldcs(reinterpret_cast<const long long*>(P.keys) + rr);
+          if (P.has_vals)
+            v[2 * j + e] = VT == AGG_I64 ? __ldcs(static_cast<const long long*>(P.vals) + rr)
+                                         : (long long)__ldcs(static_cast<const int*>(P.vals) + rr);
+        }
+      }
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < cc.n; i += THREADS) {
+    cc.key[i] = SKEY_EMPTY;
+    cc.cnt[i] = 0;
+    cc.sum[i] = 0;
+    if (Ent<ENT>::MM) {
+      cc.mn[i] = INT64_MAX;
+      cc.mx[i] = INT64_MIN;
+    }
+  }
+  __syncthreads();
+  uint64_t h[FAST_RPT];
+  bool need[FAST_RPT], cfree[FAST_RPT];
+#pragma unroll
+  for (int r = 0; r < FAST_RPT; ++r) {
+    h[r] = fmix64((uint64_t)k[r] ^ seed0);
+    cfree[r] = true;
+    bool hit = false;
+    if (valid[r]) hit = cache_hit<ENT>(cc, k[r], h[r], 1ull, (unsigned long long)v[r], v[r], v[r], cfree[r]);
+    need[r] = valid[r] && !hit;
+  }
+  // key word at every remaining row's home slot, all loads in flight together
+  uint32_t slot[FAST_RPT];
+  long long kf[FAST_RPT];
+#pragma unroll
+  for (int r = 0; r < FAST_RPT; ++r) {
+    slot[r] = fast_home(h[r], s_act);
+    kf[r] = need[r] && k[r] != EMPTY_KEY ? __ldcg(reinterpret_cast<const long long*>(Ent<ENT>::at(P.ent, slot[r])))
+                                         : EMPTY_KEY;
+  }
+#pragma unroll
+  for (int r = 0; r < FAST_RPT; ++r) {
+    if (!need[r]) continue;
+    const uint32_t sl = fast_probe<ENT>(P, s_act, k[r], h[r], slot[r], kf[r]);
+    Ent<ENT>::add(Ent<ENT>::at(P.ent, sl), P.ops, 1ull, (unsigned long long)v[r], v[r], v[r]);
+    if (cfree[r]) cache_insert(cc, S, k[r], h[r], sl);
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < cc.n; i += THREADS) {
+    const long long key = cc.key[i];
+    const unsigned long long c = cc.cnt[i];
+    if (key == SKEY_EMPTY || c == 0) continue;
+    Ent<ENT>::add(Ent<ENT>::at(P.ent, cc.slot[i]), P.ops, c, cc.sum[i], Ent<ENT>::MM ? cc.mn[i] : 0,
+                  Ent<ENT>::MM ? cc.mx[i] : 0);
+  }
+}
+
+// Emits every occupied slot among [0, s_act) (and the side slot), resetting
+// each, then the last block to finish publishes the group count.  A thread
+// reads 16 tag bytes; each warp reserves its output rows with one atomic.
+template <int ENT>
+__global__ void __launch_bounds__(EMIT_THREADS) fast_emit_kernel(const HashParams P, uint32_t s_act) {
+  Ctrl* C = P.ctrl;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t words = s_act / 4;
+  const uint64_t w0 = ((uint64_t)blockIdx.x * EMIT_THREADS + threadIdx.x) * 4;
+  uint32_t tw[4] = {0u, 0u, 0u, 0u};
+  if (w0 + 4 <= words) {
+    const uint4 t = __ldcg(reinterpret_cast<const uint4*>(P.tags + w0));
+    tw[0] = t.x;
+    tw[1] = t.y;
+    tw[2] = t.z;
+    tw[3] = t.w;
+  } else {
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) tw[q] = (w0 + q < words) ? __ldcg(P.tags + w0 + q) : 0u;
+  }
+  uint32_t oc = 0;
+#pragma unroll
+  for (uint32_t q = 0; q < 4; ++q) oc += __popc(~__vcmpeq4(tw[q], 0u) & 0x01010101u);
+  uint32_t incl = oc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
+    if ((int)lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && total) base = atomicAdd(&C->out_count, (unsigned long long)total);
+  base = __shfl_sync(FULL_MASK, base, 31);
+  unsigned long long pos = base + incl - oc;
+#pragma unroll
+  for (uint32_t q = 0; q < 4; ++q) {
+    if (tw[q] == 0) continue;
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+      if (((tw[q] >> (8 * j)) & 0xFFu) == 0) continue;
+      emit_one<ENT>(P, Ent<ENT>::at(P.ent, (uint32_t)(w0 + q) * 4 + j), pos);
+      ++pos;
+    }
+    __stcg(P.tags + w0 + q, 0u);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // the side slot of the empty-marker key
+    uint8_t* tb = reinterpret_cast<uint8_t*>(P.tags) + P.slots;
+    if (__ldcg(tb)) {
+      const unsigned long long at = atomicAdd(&C->out_count, 1ull);
+      emit_one<ENT>(P, Ent<ENT>::at(P.ent, P.slots), at);
+      __stcg(reinterpret_cast<long long*>(Ent<ENT>::at(P.ent, P.slots)), (long long)EMPTY_KEY);
+      __stcg(tb, (uint8_t)0);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  __threadfence();
+  if (atomicAdd(&C->done_count, 1u) != gridDim.x - 1) return;
+  __threadfence();
+  volatile Ctrl* V = C;
+  const unsigned long long ng = V->out_count;
+  if (P.o_ngroups) *P.o_ngroups = ng;
+  C->last_n_rows = P.n;
+  C->last_n_groups = ng;
+  C->last_levels = 1;
+  C->last_rounds = 1;
+  C->last_rows_at_full = ~0ull;
+  for (int l = 0; l < AGG_MAX_LEVELS; ++l) {
+    C->last_spill_records[l] = 0;
+    C->last_resident_groups[l] = l == 0 ? ng : 0;
+  }
+  for (int ph = 0; ph < PHASES; ++ph) C->last_phase_ns[ph] = 0;
+  C->out_count = 0;
+  __threadfence();
+  C->done_count = 0;
+}
+
+// ---- partitioned in-budget path (small inputs): no global atomics
+//
+// For a small in-budget input the table's atomics, not memory, bound the pass
+// (about four global atomics per row).  These inputs are therefore aggregated
+// the way the hybrid hash aggregates partitions that fit in memory (Section
+// 4.3), with a block's shared memory as that memory: the first launch splits
+// each block's rows by the top hash bits into np partitions, a counting sort
+// within the block written to a scratch area inside the budget (small enough
+// to stay in L2); the second launch gives each partition to one block, which
+// aggregates all of its records in its shared-memory table and writes its
+// groups straight to the output.  Keys that do not fit a block's table go to
+// the global table by linear probing (as in the fast path above), and the last
+// block to finish emits that table when it was used, then publishes the count.
+
+constexpr uint32_t PART_MAX = 2048;      // most partitions
+constexpr uint32_t PART_MAX_BLK = 512;   // most first-launch blocks (2M rows)
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+// Exclusive scan over the block of one value per thread (THREADS threads).
+__device__ __forceinline__ uint32_t block_scan_excl(uint32_t x, uint32_t* wsum, uint32_t& total) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL_MASK, inc, o);
+    if ((int)lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t t = lane < WARPS ? wsum[lane] : 0u;
+    uint32_t ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL_MASK, ti, o);
+      if ((int)lane >= o) ti += y;
+    }
+    if (lane < WARPS) wsum[lane] = ti - t;
+    if (lane == WARPS - 1) wsum[WARPS] = ti;
+  }
+  __syncthreads();
+  total = wsum[WARPS];
+  const uint32_t r = wsum[warp] + inc - x;
+  __syncthreads();
+  return r;
+}
+
+// Launch 1: block b counting-sorts its FAST_ROWS rows by partition into
+// rec[b * FAST_ROWS ...] and stores, for every partition q, its row count and
+// start in the block's run at cnt[q * nblk + b] and start[q * nblk + b].
+template <int VT>
+__global__ void __launch_bounds__(THREADS, 2) part_scatter_kernel(const HashParams P, uint32_t plog, uint32_t nblk,
+                                                               longlong2* __restrict__ rec, uint32_t* __restrict__ gcnt,
+                                                               uint32_t* __restrict__ gstart) {
+  __shared__ uint32_t cnt[PART_MAX];
+  __shared__ uint32_t wsum[WARPS + 1];
+  pdl_launch_dependents();  // the aggregation launch may start its set-up
+  const uint32_t np = 1u << plog, b = blockIdx.x;
+  const uint64_t row0 = (uint64_t)b * FAST_ROWS;
+  const uint64_t seed0 = level_seed(P.seed, 0);
+  long long k[FAST_RPT], v[FAST_RPT];
+  bool valid[FAST_RPT];
+#pragma unroll
+  for (int j = 0; j < FAST_RPT / 2; ++j) {
+    const uint64_t row = row0 + (uint64_t)j * 2 * THREADS + 2 * threadIdx.x;
+    if (P.vec_ok && row + 1 < P.n) {
+      const longlong2 kk = __ldcs(reinterpret_cast<const longlong2*>(P.keys + row));
+      k[2 * j] = kk.x;
+      k[2 * j + 1] = kk.y;
+      if (!P.has_vals) {
+        v[2 * j] = v[2 * j + 1] = 0;
+      } else if (VT == AGG_I64) {
+        const longlong2 vv = __ldcs(reinterpret_cast<const longlong2*>(static_cast<const long long*>(P.vals) + row));
+        v[2 * j] = vv.x;
+        v[2 * j + 1] = vv.y;
+      } else {
+        const int2 vv = __ldcs(reinterpret_cast<const int2*>(static_cast<const int*>(P.vals) + row));
+        v[2 * j] = vv.x;
+        v[2 * j + 1] = vv.y;
+      }
+      valid[2 * j] = valid[2 * j + 1] = true;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const uint64_t rr = row + e;
+        valid[2 * j + e] = rr < P.n;
+        k[2 * j + e] = 0;
+        v[2 * j + e] = 0;
+        if (rr < P.n) {
+          k[2 * j + e] = __ldcs(reinterpret_cast<const long long*>(P.keys) + rr);
+          if (P.has_vals)
+            v[2 * j + e] = VT == AGG_I64 ? __ldcs(static_cast<const long long*>(P.vals) + rr)
+                                         : (long long)__ldcs(static_cast<const int*>(P.vals) + rr);
+        }
+      }
+    }
+  }
+  for (uint32_t q = threadIdx.x; q < np; q += THREADS) cnt[q] = 0;
+  __syncthreads();
+  uint32_t part[FAST_RPT], rank[FAST_RPT];
+#pragma unroll
+  for (int r = 0; r < FAST_RPT; ++r) {
+    part[r] = plog ? (uint32_t)(fmix64((uint64_t)k[r] ^ seed0) >> (64 - plog)) : 0u;
+    rank[r] = valid[r] ? sh_atom_add_u32(&cnt[part[r]], 1u) : 0u;
+  }
+  __syncthreads();
+  // partition starts within the block's run: exclusive scan over np counts
+  const uint32_t per = (np + THREADS - 1) / THREADS, q0 = threadIdx.x * per;
+  uint32_t mine = 0;
+  for (uint32_t i = 0; i < per; ++i)
+    if (q0 + i < np) mine += cnt[q0 + i];
+  uint32_t total;
+  uint32_t acc = block_scan_excl(mine, wsum, total);
+  for (uint32_t i = 0; i < per; ++i) {
+    const uint32_t q = q0 + i;
+    if (q >= np) break;
+    const uint32_t c = cnt[q];
+    __stcg(gcnt + (size_t)q * nblk + b, c);
+    __stcg(gstart + (size_t)q * nblk + b, acc);
+    cnt[q] = acc;
+    acc += c;
+  }
+  __syncthreads();
+  longlong2* run = rec + (size_t)b * FAST_ROWS;
+#pragma unroll
+  for (int r = 0; r < FAST_RPT; ++r) {
+    if (!valid[r]) continue;
+    longlong2 x;
+    x.x = k[r];
+    x.y = v[r];
+    __stcg(run + cnt[part[r]] + rank[r], x);
+  }
+}
+
+// Emits the occupied slots of [0, s_act) with the whole block (rare: only
+// when keys overflowed a block's shared-memory table).
+template <int ENT>
+__device__ void block_emit_table(const HashParams& P, uint32_t s_act) {
+  Ctrl* C = P.ctrl;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t words = s_act / 4;
+  for (uint32_t w0 = threadIdx.x * 4; w0 - threadIdx.x * 4 < words; w0 += THREADS * 4) {
+    uint32_t tw[4];
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) tw[q] = (w0 + q < words) ? __ldcg(P.tags + w0 + q) : 0u;
+    uint32_t oc = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) oc += __popc(~__vcmpeq4(tw[q], 0u) & 0x01010101u);
+    uint32_t incl = oc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
+      if ((int)lane >= o) incl += y;
+    }
+    const uint32_t tot = __shfl_sync(FULL_MASK, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && tot) base = atomicAdd(&C->out_count, (unsigned long long)tot);
+    base = __shfl_sync(FULL_MASK, base, 31);
+    unsigned long long pos = base + incl - oc;
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      if (tw[q] == 0) continue;
+#pragma unroll
+      for (uint32_t j = 0; j < 4; ++j) {
+        if (((tw[q] >> (8 * j)) & 0xFFu) == 0) continue;
+        emit_one<ENT>(P, Ent<ENT>::at(P.ent, (w0 + q) * 4 + j), pos);
+        ++pos;
+      }
+      __stcg(P.tags + w0 + q, 0u);
+    }
+  }
+}
+
+// Launch 2: block q aggregates partition q.  Global table [0, s_ovf) takes the
+// keys its shared-memory table cannot hold; the empty-marker key value takes
+// the side slot.  The last block to finish emits those and publishes the run.
+template <int ENT>
+__global__ void __launch_bounds__(THREADS, 2)
+    part_agg_kernel(const HashParams P, uint32_t plog, uint32_t nblk, const longlong2* __restrict__ rec,
+                    const uint32_t* __restrict__ gcnt, const uint32_t* __restrict__ gstart, uint32_t s_ovf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t pre[PART_MAX_BLK + 1];
+  __shared__ uint32_t sst[PART_MAX_BLK];
+  __shared__ uint32_t wsum[WARPS + 1];
+  __shared__ uint32_t last;
+  Ctrl* C = P.ctrl;
+  const Cache cc = carve_cache(smem_raw + ((sizeof(Smem) + 15) & ~size_t(15)), P.ns, Ent<ENT>::MM);
+  const uint32_t q = blockIdx.x;
+  const uint64_t seed0 = level_seed(P.seed, 0);
+  for (uint32_t i = threadIdx.x; i < cc.n; i += THREADS) {
+    cc.key[i] = SKEY_EMPTY;
+    cc.cnt[i] = 0;
+    cc.sum[i] = 0;
+    if (Ent<ENT>::MM) {
+      cc.mn[i] = INT64_MAX;
+      cc.mx[i] = INT64_MIN;
+    }
+  }
+  pdl_wait();  // the partitioning launch is complete and visible
+  uint32_t c = 0;
+  if (threadIdx.x < nblk) {
+    c = __ldcg(gcnt + (size_t)q * nblk + threadIdx.x);
+    sst[threadIdx.x] = __ldcg(gstart + (size_t)q * nblk + threadIdx.x);
+  }
+  uint32_t total;
+  const uint32_t ex = block_scan_excl(c, wsum, total);  // nblk <= THREADS
+  if (threadIdx.x < nblk) pre[threadIdx.x] = ex;
+  if (threadIdx.x == 0) pre[nblk] = total;
+  __syncthreads();
+  bool ovf = false, side = false;
+  constexpr int K = 4;
+  for (uint32_t base = 0; base < total; base += THREADS * K) {
+    long long k[K], v[K];
+    bool in[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const uint32_t i = base + (uint32_t)j * THREADS + threadIdx.x;
+      in[j] = i < total;
+      k[j] = v[j] = 0;
+      if (in[j]) {
+        uint32_t lo = 0, hi = nblk;  // the run holding record i: pre[lo] <= i < pre[lo + 1]
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (pre[mid] <= i) lo = mid;
+          else hi = mid;
+        }
+        const longlong2 x = __ldcg(rec + (size_t)lo * FAST_ROWS + sst[lo] + (i - pre[lo]));
+        k[j] = x.x;
+        v[j] = x.y;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (!in[j]) continue;
+      const uint64_t h = fmix64((uint64_t)k[j] ^ seed0);
+      if (sub_upsert<ENT>(cc, k[j], h, v[j])) continue;
+      uint32_t sl = fast_home(h, s_ovf);
+      const long long k2 =
+          k[j] == EMPTY_KEY ? EMPTY_KEY : __ldcg(reinterpret_cast<const long long*>(Ent<ENT>::at(P.ent, sl)));
+      sl = fast_probe<ENT>(P, s_ovf, k[j], h, sl, k2);
+      Ent<ENT>::add(Ent<ENT>::at(P.ent, sl), P.ops, 1ull, (unsigned long long)v[j], v[j], v[j]);
+      if (k[j] == EMPTY_KEY) side = true;
+      else ovf = true;
+    }
+  }
+  if (ovf) atomicOr(&C->overflow_used[0], 1u);
+  if (side) atomicOr(&C->overflow_used[1], 1u);
+  __syncthreads();
+  sub_emit<ENT>(P, cc, 0);  // ends with a block barrier
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&C->done_count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (ld_acquire_u32(&C->overflow_used[0])) block_emit_table<ENT>(P, s_ovf);
+  if (threadIdx.x == 0 && ld_acquire_u32(&C->overflow_used[1])) {
+    uint8_t* tb = reinterpret_cast<uint8_t*>(P.tags) + P.slots;
+    if (__ldcg(tb)) {
+      const unsigned long long at = atomicAdd(&C->out_count, 1ull);
+      emit_one<ENT>(P, Ent<ENT>::at(P.ent, P.slots), at);
+      __stcg(reinterpret_cast<long long*>(Ent<ENT>::at(P.ent, P.slots)), (long long)EMPTY_KEY);
+      __stcg(tb, (uint8_t)0);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  __threadfence();
+  volatile Ctrl* V = C;
+  const unsigned long long ng = V->out_count;
+  if (P.o_ngroups) *P.o_ngroups = ng;
+  C->last_n_rows = P.n;
+  C->last_n_groups = ng;
+  C->last_levels = 1;
+  C->last_rounds = 1;
+  C->last_rows_at_full = ~0ull;
+  for (int l = 0; l < AGG_MAX_LEVELS; ++l) {
+    C->last_spill_records[l] = 0;
+    C->last_resident_groups[l] = l == 0 ? ng : 0;
+    C->resident_groups[l] = 0;
+  }
+  for (int ph = 0; ph < PHASES; ++ph) C->last_phase_ns[ph] = 0;
+  C->overflow_used[0] = 0;
+  C->overflow_used[1] = 0;
+  C->out_count = 0;
+  __threadfence();
+  C->done_count = 0;
+}
+
+template <int ENT>
+void* part_agg_ptr() {
+  return reinterpret_cast<void*>(&part_agg_kernel<ENT>);
+}
+
+void* pick_part_agg(int ent) {
+  if (ent == ENT32_CS) return part_agg_ptr<ENT32_CS>();
+  if (ent == ENT32_CSMM32) return part_agg_ptr<ENT32_CSMM32>();
+  return part_agg_ptr<ENT64>();
+}
+
+template <int ENT, int VT>
+void* fast_kernel_ptr() {
+  return reinterpret_cast<void*>(&fast_agg_kernel<ENT, VT>);
+}
+
+void* pick_fast_kernel(int ent, int vt) {
+  if (vt == AGG_I32) {
+    if (ent == ENT32_CS) return fast_kernel_ptr<ENT32_CS, AGG_I32>();
+    if (ent == ENT32_CSMM32) return fast_kernel_ptr<ENT32_CSMM32, AGG_I32>();
+    return fast_kernel_ptr<ENT64, AGG_I32>();
+  }
+  if (ent == ENT32_CS) return fast_kernel_ptr<ENT32_CS, AGG_I64>();
+  return fast_kernel_ptr<ENT64, AGG_I64>();
+}
+
 template <int ENT>
 __global__ void init_table_kernel(uint8_t* ent, uint32_t* tags, uint32_t slots) {
   // slots + 1 entries (the last is the side slot) and slots + BUCKET tag bytes
@@ -1652,6 +2188,12 @@ __global__ void init_table_kernel(uint8_t* ent, uint32_t* tags, uint32_t slots) 
   for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < (slots + BUCKET) / 4;
        w += (uint64_t)gridDim.x * blockDim.x)
     tags[w] = 0;
+}
+
+template <int ENT>
+__global__ void reset_entries_kernel(uint8_t* ent, uint64_t count) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < count; s += (uint64_t)gridDim.x * blockDim.x)
+    Ent<ENT>::reset(Ent<ENT>::at(ent, (uint32_t)s));
 }
 
 template <int ENT, int VT>
@@ -1695,6 +2237,10 @@ cudaError_t hash_kernel_info(int ent_kind, int vt, uint32_t ns, int device, Kern
   const size_t smem = smem_bytes(ent_kind, ns);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(pick_fast_kernel(ent_kind, vt), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(pick_part_agg(ent_kind), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   int per_sm = 0, sms = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, THREADS, smem);
   if (e != cudaSuccess) return e;
@@ -1735,6 +2281,84 @@ cudaError_t hash_launch(int ent_kind, int vt, const HashParams& p, const KernelI
   void* k = pick_kernel(ent_kind, vt);
   void* args[] = {const_cast<HashParams*>(&p)};
   return cudaLaunchCooperativeKernel(k, dim3(ki.blocks), dim3(THREADS), args, ki.smem, s);
+}
+
+uint32_t hash_fast_slots(uint64_t n, uint64_t slots) {
+  if (n > slots / 2) return 0;
+  uint64_t a = 2 * n > MIN_SLOTS ? 2 * n : MIN_SLOTS;
+  a = (a + BUCKET - 1) / BUCKET * BUCKET;
+  return (uint32_t)(a < slots ? a : slots);
+}
+
+cudaError_t hash_fast_launch(int ent_kind, int vt, const HashParams& p, uint32_t s_act, size_t smem, cudaStream_t s) {
+  if (p.n > 0) {
+    const unsigned grid = (unsigned)((p.n + FAST_ROWS - 1) / FAST_ROWS);
+    void* args[] = {const_cast<HashParams*>(&p), &s_act};
+    const cudaError_t e = cudaLaunchKernel(pick_fast_kernel(ent_kind, vt), dim3(grid), dim3(THREADS), args, smem, s);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned eg = (unsigned)((s_act + EMIT_SLOTS - 1) / EMIT_SLOTS);
+  if (ent_kind == ENT32_CS) fast_emit_kernel<ENT32_CS><<<eg, EMIT_THREADS, 0, s>>>(p, s_act);
+  else if (ent_kind == ENT32_CSMM32) fast_emit_kernel<ENT32_CSMM32><<<eg, EMIT_THREADS, 0, s>>>(p, s_act);
+  else fast_emit_kernel<ENT64><<<eg, EMIT_THREADS, 0, s>>>(p, s_act);
+  return cudaGetLastError();
+}
+
+bool hash_part_plan(uint64_t n, uint64_t slots, uint32_t es, uint32_t ns, PartPlan* out) {
+  if (n == 0 || n > (uint64_t)PART_MAX_BLK * FAST_ROWS || ns < 256) return false;
+  PartPlan pp;
+  pp.nblk = (uint32_t)((n + FAST_ROWS - 1) / FAST_ROWS);
+  uint32_t plog = 0;
+  while ((1ull << plog) * ns < n && (1u << plog) < PART_MAX) ++plog;  // about ns rows per partition
+  pp.plog = plog;
+  uint64_t ovf = n + n / 4 > MIN_SLOTS ? n + n / 4 : MIN_SLOTS;  // at most n keys overflow: always room
+  ovf = (ovf + BUCKET - 1) / BUCKET * BUCKET;
+  pp.s_ovf = (uint32_t)ovf;
+  const uint64_t rec_bytes = (uint64_t)pp.nblk * FAST_ROWS * 16;
+  const uint64_t idx_bytes = 2ull * ((uint64_t)pp.nblk << plog) * 4;
+  const uint64_t scratch_slots = (rec_bytes + idx_bytes + 256 + es - 1) / es + 8;
+  if (ovf + 1 + scratch_slots > slots) return false;  // the overflow table, then its side slot, stay clear
+  pp.scratch_slot = (uint32_t)(slots - scratch_slots);  // scratch at the top of the entry memory
+  *out = pp;
+  return true;
+}
+
+cudaError_t hash_part_launch(int ent_kind, int vt, const HashParams& p, const PartPlan& pp, uint32_t es, size_t smem,
+                             cudaStream_t s) {
+  uint8_t* base = p.ent + (size_t)pp.scratch_slot * es;
+  base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(base) + 255) & ~uintptr_t(255));
+  longlong2* rec = reinterpret_cast<longlong2*>(base);
+  uint32_t* gcnt = reinterpret_cast<uint32_t*>(base + (size_t)pp.nblk * FAST_ROWS * 16);
+  uint32_t* gstart = gcnt + ((size_t)pp.nblk << pp.plog);
+  uint32_t plog = pp.plog, nblk = pp.nblk, s_ovf = pp.s_ovf;
+  if (vt == AGG_I32) part_scatter_kernel<AGG_I32><<<nblk, THREADS, 0, s>>>(p, plog, nblk, rec, gcnt, gstart);
+  else part_scatter_kernel<AGG_I64><<<nblk, THREADS, 0, s>>>(p, plog, nblk, rec, gcnt, gstart);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1u << plog);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const longlong2* crec = rec;
+  const uint32_t* ccnt = gcnt;
+  const uint32_t* cstart = gstart;
+  void* args[] = {const_cast<HashParams*>(&p), &plog, &nblk, &crec, &ccnt, &cstart, &s_ovf};
+  return cudaLaunchKernelExC(&cfg, pick_part_agg(ent_kind), args);
+}
+
+cudaError_t hash_reset_entries(uint8_t* ent, uint64_t count, int ent_kind, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((count + 255) / 256 > 4096 ? 4096 : (count + 255) / 256);
+  if (ent_kind == ENT32_CS) reset_entries_kernel<ENT32_CS><<<blocks, 256, 0, s>>>(ent, count);
+  else if (ent_kind == ENT32_CSMM32) reset_entries_kernel<ENT32_CSMM32><<<blocks, 256, 0, s>>>(ent, count);
+  else reset_entries_kernel<ENT64><<<blocks, 256, 0, s>>>(ent, count);
+  return cudaGetLastError();
 }
 
 cudaError_t hash_init_table(uint8_t* ent, uint32_t* tags, uint32_t slots, int ent_kind, cudaStream_t s) {

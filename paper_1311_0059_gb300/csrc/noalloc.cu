@@ -11,8 +11,12 @@
 // which every GPU that loads this library holds until the process exits.
 //
 // The array has room for AGG_NOALLOC_SLOTS table slots; inputs are limited to
-// AGG_NOALLOC_MAX_ROWS rows, so that every group stays resident (a bucket of 32
-// slots holds on average at most 8 keys) and nothing needs a staging area.
+// AGG_NOALLOC_MAX_ROWS rows, at most a quarter of the slots.  The group-by runs
+// on the in-budget path: rows are split by hash into partitions that blocks
+// aggregate in shared memory, and a key that does not fit there probes linearly
+// across the table's active slots, so every distinct key finds a place whatever
+// its hash (even for key sets built to collide) and nothing ever needs a
+// staging area.  The partitions' scratch records use the top of the entries.
 // All calls share the one array: calls whose work overlaps on the GPU race on
 // it and must be ordered by the caller (one stream, or events).
 #include <mutex>
@@ -116,13 +120,22 @@ extern "C" agg_status agg_run_noalloc(const agg_spec* spec, const int64_t* d_key
   if (st != AGG_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int ent = entry_kind(spec->ops, spec->value_type);
+  // n <= AGG_NOALLOC_MAX_ROWS, a quarter of the slots: an in-budget path always
+  // applies (the partitioned one, whose scratch sits at the top of the entries,
+  // or for n = 0 the plain one, which then only publishes the empty result)
+  const uint32_t es = entry_bytes(ent);
+  PartPlan pp;
+  const bool part = hash_part_plan(n, NA_SLOTS, es, 2048, &pp);
+  const uint32_t s_act = part ? pp.s_ovf : hash_fast_slots(n, NA_SLOTS);
+  if (s_act == 0) return AGG_ERR_INTERNAL;
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(d->base);
   uint32_t* tags = reinterpret_cast<uint32_t*>(d->base + NA_CTRL);
   uint8_t* ents = d->base + NA_CTRL + NA_TAGS;
-  // The array keeps the previous call's contents: start from a clear control
-  // block and an empty table.
+  // The array keeps the previous call's contents: clear the control block and
+  // the part of the table this call uses (its s_act slots, then the side slot
+  // of the empty-marker key right after them).
   if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess ||
-      hash_init_table(ents, tags, NA_SLOTS, ent, s) != cudaSuccess) {
+      hash_init_table(ents, tags, s_act, ent, s) != cudaSuccess) {
     cudaGetLastError();
     return AGG_ERR_CUDA;
   }
@@ -143,34 +156,32 @@ extern "C" agg_status agg_run_noalloc(const agg_spec* spec, const int64_t* d_key
   p.ctrl = ctrl;
   p.ent = ents;
   p.tags = tags;
-  p.slots = NA_SLOTS;
-  // no staging: every group is resident (a spill would be reported, not written)
+  p.slots = s_act;  // the side slot follows the active slots
   p.seed = spec->seed;
   p.ops = spec->ops;
   p.fan_log2 = 4;
   p.lf = 0.5;
-  p.s_act0 = NA_SLOTS;
+  p.s_act0 = s_act;
   p.ns = 2048;
   p.cache = 1;
   p.dedup = 0;
   p.timeout_ns = 4000000000ull;
-  if (hash_launch(ent, spec->value_type, p, d->ki[ent][spec->value_type], s) != cudaSuccess) {
+  const size_t smem = d->ki[ent][spec->value_type].smem;
+  if ((part ? hash_part_launch(ent, spec->value_type, p, pp, es, smem, s)
+            : hash_fast_launch(ent, spec->value_type, p, s_act, smem, s)) != cudaSuccess) {
     cudaGetLastError();
     return AGG_ERR_CUDA;
   }
-  if (cudaStreamSynchronize(s) != cudaSuccess) {
-    cudaGetLastError();
-    return AGG_ERR_CUDA;
-  }
+  // The run's status and group count, read in stream order on the caller's
+  // stream (copies to pageable host memory return once they are complete).
   unsigned long long bits = 0, ng = 0;
-  if (cudaMemcpy(&bits, &ctrl->status_bits, 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(&ng, &ctrl->last_n_groups, 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+  if (cudaMemcpyAsync(&bits, &ctrl->status_bits, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&ng, &ctrl->last_n_groups, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return AGG_ERR_CUDA;
   }
   if (n_groups) *n_groups = ng;
-  if (bits & (1ull << (int)AGG_ERR_TIMEOUT)) return AGG_ERR_TIMEOUT;
-  if (bits & (1ull << (int)AGG_ERR_STAGING_EXHAUSTED)) return AGG_ERR_STAGING_EXHAUSTED;
   if (bits & (1ull << (int)AGG_ERR_OUTPUT_CAPACITY)) return AGG_ERR_OUTPUT_CAPACITY;
   if (bits) return AGG_ERR_INTERNAL;
   return AGG_OK;

@@ -79,3 +79,29 @@ def test_tuning_limits_are_checked_on_the_host(lib):
         with pytest.raises(_abi.AggError) as e:
             gb.plan(64 << 20, 1000, spec, t)
         assert e.value.status == _abi.AGG_ERR_INVALID_ARG
+
+
+def test_plan_picks_the_in_budget_paths(lib):
+    # A table that can hold every row's key at once (n at most half the slots)
+    # completes in place: small inputs go to the partitioned path (partitions of
+    # about one shared-memory table, 2048 entries), larger ones to the single
+    # table; more rows than that, or the knob set to off, give the spilling path.
+    from paper_1311_0059_gb300 import groupby as gb, _abi
+    spec32 = gb.make_spec(ops=15, value_type=_abi.AGG_I32)
+    p = gb.plan(64 << 20, 1_000_000, spec32)        # the plain 1M-row, 10k-key workload
+    assert p["in_budget_path"] == 1 and p["partitions"] == 512 and p["staging_bytes"] == 0
+    assert p["active_slots"] >= 1_250_000             # room for every key if all overflowed
+    spec = gb.make_spec(ops=3, value_type=_abi.AGG_I64)
+    p = gb.plan(256 << 20, 3_000_000, spec)           # past the partitioned path's 2M rows
+    assert p["in_budget_path"] == 2 and p["active_slots"] >= 6_000_000
+    p = gb.plan(256 << 20, 200_000_000, gb.make_spec(ops=15, value_type=_abi.AGG_I64))
+    assert p["in_budget_path"] == 0 and p["staging_bytes"] > 0
+    p = gb.plan(64 << 20, 1_000_000, spec32, _abi.agg_tuning(in_budget=2))
+    assert p["in_budget_path"] == 0
+    p = gb.plan(64 << 20, 1_000_000, spec32, _abi.agg_tuning(smem_entries=1))
+    assert p["in_budget_path"] == 2                   # no shared-memory tables: the single table
+    assert gb.plan(1 << 20, 0, spec)["in_budget_path"] == 2   # empty input: only the empty result
+    # the sort path never takes them
+    assert gb.plan(64 << 20, 1000, gb.make_spec(ops=15, path=_abi.AGG_PATH_SORT))["in_budget_path"] == 0
+    with pytest.raises(_abi.AggError):
+        gb.plan(64 << 20, 10, spec, _abi.agg_tuning(in_budget=3))

@@ -2,7 +2,9 @@
 out must end the run with AGG_ERR_TIMEOUT, and the handle must work again.
 
 Every grid barrier of the hash kernel waits with a limit (agg_tuning
-.wait_limit_us; 4 s by default).  A limit of 1 us makes the waits run out: on an
+.wait_limit_us; 4 s by default).  The input would fit the table at once, so
+the in-budget paths (which have no grid barrier) are turned off to run it
+through the spilling kernel.  A limit of 1 us makes the waits run out: on an
 input of a few tiles most blocks draw no tile and reach the first grid barrier
 microseconds before the busy blocks arrive, and one arrival of 304 blocks at a
 barrier already takes about that long.  Nothing hangs and nothing faults: each
@@ -28,7 +30,7 @@ def test_bounded_wait_runs_out_and_the_handle_recovers(oracle):
     vals = rng.integers(-2**40, 2**40, keys.size, dtype=np.int64)
     exp = oracle_expected(oracle, keys, vals)
     dk, dv = to_dev(keys), to_dev(vals)
-    with GroupBy(4 * MB, tuning=agg_tuning(wait_limit_us=1)) as g:
+    with GroupBy(4 * MB, tuning=agg_tuning(wait_limit_us=1, in_budget=2)) as g:
         timed_out = False
         for _ in range(5):
             try:
@@ -40,7 +42,7 @@ def test_bounded_wait_runs_out_and_the_handle_recovers(oracle):
             # a run whose waits all ended in time is a correct run
             assert_parity(got, exp, what="a run within the 1 us limit")
         assert timed_out, "no wait ran out with a limit of 1 us"
-        g.set_tuning(agg_tuning())  # the default limit again
+        g.set_tuning(agg_tuning(in_budget=2))  # the default limit again
         for _ in range(2):
             got = canon({k: t.cpu().numpy() for k, t in g.run(dk, dv).items()})
             assert_parity(got, exp, what="after the timed-out run")

@@ -123,3 +123,71 @@ def test_served_rejects_pointers_the_kernel_cannot_use():
     info = srv.poll(t)
     assert info.state == _abi.AGG_QUERY_DONE and info.status == 0 and info.n_groups == 1000
     srv.close()
+
+
+def test_served_failed_launch_frees_its_ranges_only_after_its_stream(oracle, monkeypatch):
+    # The server's test hook AGG_INJECT_LAUNCH_FAILURE=k makes the k-th launch
+    # fail on the host after its control-block clear and table set-up were
+    # queued on the slot's stream.  The failed query must free its pool ranges
+    # only once that queued work is done, and the queries admitted after it
+    # (into the same ranges) must still give the oracle's result.
+    from paper_1311_0059_gb300 import _abi
+    from paper_1311_0059_gb300.groupby import Output, Server
+    monkeypatch.setenv("AGG_INJECT_LAUNCH_FAILURE", "2")
+    srv = Server(8 * MB, max_active=1)
+    ws = [dg.Workload(f"q{i}", n=150_000, domain=40_000, seed=20 + i, budget=6 * MB) for i in range(4)]
+    data, ts = [], []
+    for w in ws:
+        k, v = w.host()
+        o = Output(w.n, 15, "cuda")
+        ts.append(srv.submit(to_dev(k), to_dev(v), w.budget, o))
+        data.append((k, v, o))
+    deadline = time.perf_counter() + 60
+    while srv.stats()["completed"] < len(ws) and time.perf_counter() < deadline:
+        srv.progress()
+    st = srv.stats()
+    assert st["completed"] == len(ws) and st["pool_in_use"] == 0 and st["staging_in_use"] == 0
+    assert st["blocks_in_use"] == 0
+    infos = [srv.poll(t) for t in ts]
+    assert infos[1].state == _abi.AGG_QUERY_FAILED and infos[1].status == _abi.AGG_ERR_CUDA
+    for i in (0, 2, 3):
+        assert infos[i].state == _abi.AGG_QUERY_DONE and infos[i].status == 0
+        k, v, o = data[i]
+        got = canon({f: x.cpu().numpy() for f, x in o.result(infos[i].n_groups).items()})
+        assert_parity(got, oracle_expected(oracle, k, v), what=f"query {i} after an injected launch failure")
+    srv.close()
+
+
+def test_served_teams_never_exceed_the_resident_blocks(oracle):
+    # Many concurrent queries whose wanted teams add up to several times the
+    # blocks the GPU holds at once: admission must keep the running teams within
+    # one co-resident wave (no cooperative grid waits on another, so no bounded
+    # wait runs out), and every result must equal the oracle's.
+    from paper_1311_0059_gb300 import _abi
+    from paper_1311_0059_gb300.groupby import Output, Server
+    srv = Server(512 * MB, max_active=32)
+    ws = [dg.Workload(f"t{i}", n=n, domain=max(n // 8, 1), seed=40 + i, budget=8 * MB)
+          for i, n in enumerate([3_000_000, 2_500_000, 4_000_000, 50_000, 3_500_000, 20_000, 2_000_000,
+                                 60_000, 3_000_000, 10_000, 2_200_000, 80_000])]
+    data, ts = [], []
+    for w in ws:
+        k, v = w.host()
+        o = Output(w.n, 15, "cuda")
+        ts.append(srv.submit(to_dev(k), to_dev(v), w.budget, o))
+        data.append((k, v, o))
+    peak_blocks = 0
+    deadline = time.perf_counter() + 120
+    while srv.stats()["completed"] < len(ws) and time.perf_counter() < deadline:
+        srv.progress()
+        st = srv.stats()
+        peak_blocks = max(peak_blocks, st["blocks_in_use"])
+        assert st["blocks_in_use"] <= st["blocks"]
+    st = srv.stats()
+    assert st["completed"] == len(ws) and st["max_concurrent"] >= 2
+    assert peak_blocks <= st["blocks"]
+    for t, (k, v, o) in zip(ts, data):
+        info = srv.poll(t)
+        assert info.state == _abi.AGG_QUERY_DONE and info.status == 0, f"ticket {t}: status {info.status}"
+        got = canon({f: x.cpu().numpy() for f, x in o.result(info.n_groups).items()})
+        assert_parity(got, oracle_expected(oracle, k, v), what=f"ticket {t} among concurrent big teams")
+    srv.close()
