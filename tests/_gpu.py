@@ -63,10 +63,17 @@ def oracle_expected(oracle, keys, vals):
     return res
 
 
-def check_invariants(res, n, vals_sum_u64=None):
+def check_invariants(res, n, vals_sum_u64=None, global_min=None, global_max=None):
+    """Invariants of any group-by result (sorted by key): COUNTs add up to n,
+    SUMs to the sum of all values (mod 2**64), the smallest MIN and largest MAX
+    are the global minimum and maximum of the values, and keys are unique."""
     assert int(np.asarray(res["count"]).astype(np.uint64).sum(dtype=np.uint64)) == n
     if vals_sum_u64 is not None and "sum" in res:
         assert np.asarray(res["sum"]).view(np.uint64).sum(dtype=np.uint64) == vals_sum_u64
+    if global_min is not None and "min" in res and n:
+        assert int(np.asarray(res["min"]).min()) == global_min, "smallest MIN is not the global minimum"
+    if global_max is not None and "max" in res and n:
+        assert int(np.asarray(res["max"]).max()) == global_max, "largest MAX is not the global maximum"
     k = np.asarray(res["keys"])
     assert np.all(np.diff(k) > 0), "duplicate or unsorted group keys"
 
