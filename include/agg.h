@@ -95,7 +95,10 @@ typedef struct agg_tuning {
   uint32_t in_budget;      /* in-budget paths for inputs whose every group fits the table at once
                               (n at most half the slots): 0 = default (on), 2 = off (always the
                               spilling path).  Results do not depend on it */
-  uint32_t reserved;       /* must be 0 */
+  uint32_t sorted_input;   /* sorted-input path (Section 6.4: sort-based aggregation wins on sorted
+                              data): a sampled order check, then one segmented reduction with no
+                              table when the keys are non-decreasing.  0 = default (on), 2 = off.
+                              Results do not depend on it */
 } agg_tuning;
 
 /* Output arrays, device pointers owned by the caller, one row per group.
@@ -135,6 +138,7 @@ typedef struct agg_stats {
                                                     barrier wait, level-0 emit, partition lists, round
                                                     aggregation, barrier waits, round emit, total,
                                                     shared-memory rounds: count, scatter, aggregate */
+  uint64_t sorted_input;                         /* 1 when the run took the sorted-input path */
 } agg_stats;
 
 /* Planner output (host-only arithmetic, no GPU needed). */

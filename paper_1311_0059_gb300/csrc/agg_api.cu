@@ -103,6 +103,7 @@ agg_tuning effective(const agg_tuning* t) {
   e.fudge = (t && t->fudge > 0) ? t->fudge : DEFAULT_FUDGE;
   e.wait_limit_us = t ? t->wait_limit_us : 0;
   e.in_budget = (t && t->in_budget) ? t->in_budget : 1;  // on unless asked off
+  e.sorted_input = (t && t->sorted_input) ? t->sorted_input : 1;
   return e;
 }
 
@@ -116,7 +117,7 @@ bool valid_tuning(const agg_tuning* t) {
   if (t->warp_dedup > 2) return false;
   if (t->wait_limit_us > MAX_WAIT_LIMIT_US) return false;
   if (t->fudge < 0 || t->fudge > 16) return false;
-  if (t->in_budget > 2 || t->reserved != 0) return false;
+  if (t->in_budget > 2 || t->sorted_input > 2) return false;
   return true;
 }
 
@@ -523,6 +524,9 @@ agg_status hash_enqueue(agg_handle* h, const int64_t* d_keys, const void* d_vals
   p.cache = h->tune.smem_entries != 1;
   p.dedup = h->tune.warp_dedup == 1 ? 1 : 0;
   p.no_prefetch = host_input ? 1 : 0;
+  // the sorted-input path combines block boundaries with atomics on the output
+  // rows: device outputs only
+  p.sorted_probe = !host_input && h->tune.sorted_input != 2 && h->ki.blocks <= MAX_GRID ? 1 : 0;
   p.timeout_ns = h->tune.wait_limit_us ? 1000ull * h->tune.wait_limit_us : TIMEOUT_NS;
   // entries this run needs clear: the overflow table, the fast table, or all
   const uint64_t need_clear = part ? pp.s_ovf + 1ull : s_fast ? (uint64_t)s_fast : h->slots;
@@ -660,6 +664,7 @@ agg_status agg_get_stats(agg_handle* h, agg_stats* s) {
   s->fan_out = plan_fan(&h->spec, h->tune, c.last_n_rows, h->budget, h->es);
   s->status_bits = c.status_bits;
   s->kernel_launches = h->launches + sort_launches(h->sort);
+  s->sorted_input = c.last_sorted;
   if (h->spec.path == AGG_PATH_SORT) sort_fill_stats(h->sort, s);
   return AGG_OK;
 }

@@ -34,6 +34,7 @@ constexpr uint64_t ROUND_CAP_MAX = (uint64_t)AGG_ROUND_CAP_M << 20;  // records 
 // 1/GTABLE_DIV of the slots; the rest of the entry memory is round scratch.
 constexpr uint32_t GTABLE_DIV = AGG_GTABLE_DIV;
 constexpr uint64_t REC_BYTES = 16;         // spilled record: (int64 key, int64 value)
+constexpr int MAX_GRID = 1024;             // most blocks of one team (the sorted-input path counts per block)
 // One tile adds at most TILE rows to a partition, so at most one new chunk is
 // opened per partition per tile.
 static_assert(TILE == (int)CH, "a tile is one staging chunk");
@@ -73,6 +74,9 @@ struct alignas(128) Ctrl {
   unsigned long long lvl_sub_groups[2];   // groups they formed (keys-per-record estimate)
   unsigned int overflow_used[2];          // a key of the level (by parity) went to the global table
   unsigned int sub_next[2];               // pass C: sub-partitions claimed so far (by round parity)
+  unsigned int sorted_fail;               // sorted-input path: a key below its predecessor was found
+  unsigned int sorted_used;               // sorted-input path: this run completed on it
+  unsigned long long sorted_heads[MAX_GRID];  // sorted-input path: segment heads in each block's rows
   // ---- snapshot of the last completed run
   unsigned long long last_n_rows;
   unsigned long long last_n_groups;
@@ -82,6 +86,7 @@ struct alignas(128) Ctrl {
   unsigned long long last_phase_ns[PHASES];
   unsigned long long last_spill_records[AGG_MAX_LEVELS];
   unsigned long long last_resident_groups[AGG_MAX_LEVELS];
+  unsigned long long last_sorted;         // 1 when the last run took the sorted-input path
 };
 
 // Everything one hash-path kernel launch needs (passed by value).
@@ -116,6 +121,7 @@ struct HashParams {
   uint32_t dedup;      // warp-level key dedup on/off
   uint32_t cache;      // shared-memory cache of resident groups on/off
   uint32_t no_prefetch;  // input in host memory: no bulk L2 prefetch of input tiles
+  uint32_t sorted_probe; // try the sorted-input path first (a sampled order check decides)
   uint64_t timeout_ns; // bounded waits give up after this long
 };
 

@@ -155,6 +155,18 @@ struct Smem {
   uint32_t sub_q[2];            // pass C: sub-partitions claimed by this block, by iteration parity
   uint32_t tl_chunk[TLIST];     // staged tiles of a round pass: chunk id
   uint32_t tl_count[TLIST];     // and its record count
+  // sorted-input path: per-warp totals of a segmented scan, the carry into the
+  // next tile, and the block's leading partial segment
+  unsigned long long sw_c[WARPS], sw_s[WARPS];
+  long long sw_mn[WARPS], sw_mx[WARPS];
+  uint32_t sw_f[WARPS];
+  unsigned long long tc_c, tc_s;
+  long long tc_mn, tc_mx;
+  uint32_t tc_f;
+  unsigned long long lead_c, lead_s;
+  long long lead_mn, lead_mx;
+  uint32_t lead_valid;
+  uint32_t vote;
 };
 
 // Shared-memory table of partial states.  Counts are 32-bit (an entry is
@@ -1301,6 +1313,9 @@ __device__ void final_step(const HashParams& P, const Team& T, uint32_t levels) 
     C->last_phase_ns[ph] = V->phase_ns[ph];
     C->phase_ns[ph] = 0;
   }
+  C->last_sorted = V->sorted_used;
+  C->sorted_used = 0;
+  C->sorted_fail = 0;
   C->occupancy = 0;
   C->out_count = 0;
   C->pool_next[0] = 0;
@@ -1318,6 +1333,284 @@ __device__ void final_step(const HashParams& P, const Team& T, uint32_t levels) 
   C->done_count = 0;
 }
 
+
+// ---------------------------------------------------------------- sorted-input path
+
+// Sort-based aggregation needs no table when its input is already sorted
+// (Section 6.4: on sorted data the Sort-based algorithm wins, its sort phase
+// degenerating to a scan).  The persistent kernel therefore first checks a
+// sample: every block reads the same THREADS evenly spaced adjacent key pairs
+// and the order of the pairs' first keys, so all blocks reach the same verdict
+// with no barrier.  If the sample is in order the run tries the sorted path,
+// on contiguous row ranges, one per block:
+//   S1  each block checks its rows are non-decreasing and counts the segment
+//       heads (a row whose key differs from its predecessor's); a descent
+//       anywhere sets a flag, and after a grid barrier every block falls back
+//       to the hash path;
+//   S2  each block's first output row is the number of heads before its range;
+//   S3  a block-wide segmented scan of (COUNT, SUM, MIN, MAX), carried from
+//       tile to tile, gives each segment's aggregate at its last row, which is
+//       stored at the segment's head rank when the head lies in the block; a
+//       segment that starts in an earlier block leaves its partial aggregate
+//       (the block's leading partial) aside;
+//   S4  after a grid barrier, each leading partial is added to its segment's
+//       row with atomics (COUNT and SUM added, MIN and MAX combined).
+// The output is in ascending key order.
+
+struct Seg {
+  unsigned long long c, s;
+  long long mn, mx;
+  uint32_t f;  // the span holds a segment head
+};
+
+__device__ __forceinline__ Seg seg_identity() { return Seg{0ull, 0ull, INT64_MAX, INT64_MIN, 0u}; }
+
+// a followed by b
+__device__ __forceinline__ Seg seg_combine(const Seg& a, const Seg& b) {
+  if (b.f) return b;
+  return Seg{a.c + b.c, a.s + b.s, a.mn < b.mn ? a.mn : b.mn, a.mx > b.mx ? a.mx : b.mx, a.f};
+}
+
+__device__ __forceinline__ Seg seg_shfl_up(const Seg& x, int o) {
+  return Seg{__shfl_up_sync(FULL_MASK, x.c, o), __shfl_up_sync(FULL_MASK, x.s, o), __shfl_up_sync(FULL_MASK, x.mn, o),
+             __shfl_up_sync(FULL_MASK, x.mx, o), __shfl_up_sync(FULL_MASK, x.f, o)};
+}
+
+// The same sample in every block: true when it shows no descent.
+__device__ __noinline__ bool sorted_sample(const HashParams& P, Smem& S) {
+  const uint64_t n = P.n;
+  const uint64_t j = (n - 2) * threadIdx.x / (THREADS - 1);  // 0 .. n-2
+  const long long a = __ldcg(P.keys + j), b = __ldcg(P.keys + j + 1);
+  bool ok = a <= b;
+  const long long nb = __shfl_down_sync(FULL_MASK, a, 1);
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane < 31) ok = ok && a <= nb;
+  if (lane == 0) S.sw_mn[warp] = a;
+  __syncthreads();
+  if (lane == 31 && warp + 1 < WARPS) ok = ok && a <= S.sw_mn[warp + 1];
+  return __syncthreads_and(ok) != 0;
+}
+
+template <int VT>
+__device__ __forceinline__ void sorted_load(const HashParams& P, uint64_t row, uint64_t r1, long long (&k)[4],
+                                            long long (&v)[4], bool with_vals) {
+  if (P.vec_ok && row + 3 < r1) {
+    const longlong2 k01 = __ldcs(reinterpret_cast<const longlong2*>(P.keys + row));
+    const longlong2 k23 = __ldcs(reinterpret_cast<const longlong2*>(P.keys + row + 2));
+    k[0] = k01.x;
+    k[1] = k01.y;
+    k[2] = k23.x;
+    k[3] = k23.y;
+    if (!with_vals || !P.has_vals) {
+      v[0] = v[1] = v[2] = v[3] = 0;
+    } else if (VT == AGG_I64) {
+      const longlong2 v01 = __ldcs(reinterpret_cast<const longlong2*>(static_cast<const long long*>(P.vals) + row));
+      const longlong2 v23 = __ldcs(reinterpret_cast<const longlong2*>(static_cast<const long long*>(P.vals) + row + 2));
+      v[0] = v01.x;
+      v[1] = v01.y;
+      v[2] = v23.x;
+      v[3] = v23.y;
+    } else {
+      const int2 v01 = __ldcs(reinterpret_cast<const int2*>(static_cast<const int*>(P.vals) + row));
+      const int2 v23 = __ldcs(reinterpret_cast<const int2*>(static_cast<const int*>(P.vals) + row + 2));
+      v[0] = v01.x;
+      v[1] = v01.y;
+      v[2] = v23.x;
+      v[3] = v23.y;
+    }
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    k[j] = 0;
+    v[j] = 0;
+    if (row + j < r1) {
+      k[j] = __ldcs(P.keys + row + j);
+      if (with_vals && P.has_vals)
+        v[j] = VT == AGG_I64 ? __ldcs(static_cast<const long long*>(P.vals) + row + j)
+                             : (long long)__ldcs(static_cast<const int*>(P.vals) + row + j);
+    }
+  }
+}
+
+// Returns 1 when the run completed on the sorted path, 0 when the input is
+// not sorted (nothing was written; the hash path must run), -1 when a bounded
+// wait gave up.
+template <int ENT, int VT>
+__device__ __noinline__ int sorted_groupby(const HashParams& P, const Team& T, Smem& S) {
+  Ctrl* C = P.ctrl;
+  const uint64_t n = P.n;
+  const uint64_t per = (((n + T.nb - 1) / T.nb) + 3) & ~3ull;  // rows per block, a multiple of 4
+  const uint64_t r0 = (uint64_t)T.bid * per < n ? (uint64_t)T.bid * per : n;
+  const uint64_t r1 = r0 + per < n ? r0 + per : n;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  // ---- S1: order check and segment heads of this block's rows
+  uint32_t heads = 0;
+  bool bad = false;
+  for (uint64_t t0 = r0; t0 < r1; t0 += TILE) {
+    if (threadIdx.x == 0 && t0 + TILE < r1)
+      prefetch_l2(P.keys + t0 + TILE, (uint32_t)((r1 - t0 - TILE < (uint64_t)TILE ? r1 - t0 - TILE : TILE) * 8));
+    const uint64_t row = t0 + 4ull * threadIdx.x;
+    if (row >= r1) continue;
+    long long k[4], v[4];
+    sorted_load<VT>(P, row, r1, k, v, false);
+    long long prev = row > 0 ? __ldcg(P.keys + row - 1) : 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (row + j >= r1) break;
+      if (row + j == 0 || k[j] != prev) ++heads;
+      if (row + j > 0 && k[j] < prev) bad = true;
+      prev = k[j];
+    }
+  }
+  uint32_t total;
+  block_exclusive_scan(heads, total, S);
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    C->sorted_heads[T.bid] = total;
+    if (bad) atomicOr(&C->sorted_fail, 1u);
+  }
+  if (!grid_barrier(T, C, P.timeout_ns, S)) return -1;
+  if (ld_acquire_u32(&C->sorted_fail)) return 0;
+
+  // ---- S2: rows of the output before this block's range
+  unsigned long long before = 0, all = 0;
+  for (uint32_t b = threadIdx.x; b < T.nb; b += THREADS) {
+    const unsigned long long h = __ldcg(&C->sorted_heads[b]);
+    all += h;
+    if (b < T.bid) before += h;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    before += __shfl_down_sync(FULL_MASK, before, o);
+    all += __shfl_down_sync(FULL_MASK, all, o);
+  }
+  if (lane == 0) {
+    S.sw_c[warp] = before;
+    S.sw_s[warp] = all;
+  }
+  if (threadIdx.x == 0) {
+    S.tc_c = S.tc_s = 0;
+    S.tc_mn = INT64_MAX;
+    S.tc_mx = INT64_MIN;
+    S.tc_f = 0;
+    S.lead_valid = 0;
+  }
+  __syncthreads();
+  unsigned long long base = 0, n_groups = 0;
+  for (int w = 0; w < WARPS; ++w) {
+    base += S.sw_c[w];
+    n_groups += S.sw_s[w];
+  }
+  __syncthreads();
+
+  // ---- S3: segmented reduction, tile by tile
+  unsigned long long tile_heads = 0;  // heads of this block before the current tile
+  for (uint64_t t0 = r0; t0 < r1; t0 += TILE) {
+    if (threadIdx.x == 0 && t0 + TILE < r1) {
+      const uint64_t nr = r1 - t0 - TILE < (uint64_t)TILE ? r1 - t0 - TILE : TILE;
+      prefetch_l2(P.keys + t0 + TILE, (uint32_t)(nr * 8));
+      if (P.has_vals)
+        prefetch_l2(static_cast<const char*>(P.vals) + (t0 + TILE) * (VT == AGG_I64 ? 8 : 4),
+                    (uint32_t)(nr * (VT == AGG_I64 ? 8 : 4)));
+    }
+    const uint64_t row = t0 + 4ull * threadIdx.x;
+    long long k[4] = {0, 0, 0, 0}, v[4] = {0, 0, 0, 0};
+    bool valid[4], head[4], last[4];
+    if (row < r1) sorted_load<VT>(P, row, r1, k, v, true);
+    const long long prev = row > 0 && row < r1 ? __ldcg(P.keys + row - 1) : 0;
+    const long long next = row + 4 < n ? __ldcg(P.keys + row + 4) : 0;
+    uint32_t my_heads = 0;
+    Seg x = seg_identity();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      valid[j] = row + j < r1;
+      head[j] = valid[j] && (row + j == 0 || k[j] != (j == 0 ? prev : k[j - 1]));
+      const bool at_end = row + j + 1 >= r1;
+      last[j] = valid[j] && (at_end || (j < 3 ? k[j + 1] != k[j] : next != k[j]));
+      my_heads += head[j];
+      if (valid[j]) x = seg_combine(x, Seg{1ull, (unsigned long long)v[j], v[j], v[j], head[j] ? 1u : 0u});
+    }
+    uint32_t tile_total;
+    const uint32_t head_off = block_exclusive_scan(my_heads, tile_total, S);
+    // warp scan of the thread spans, then across warps
+    Seg xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const Seg y = seg_shfl_up(xi, o);
+      if ((int)lane >= o) xi = seg_combine(y, xi);
+    }
+    Seg ex = seg_shfl_up(xi, 1);
+    if (lane == 0) ex = seg_identity();
+    if (lane == 31) {
+      S.sw_c[warp] = xi.c;
+      S.sw_s[warp] = xi.s;
+      S.sw_mn[warp] = xi.mn;
+      S.sw_mx[warp] = xi.mx;
+      S.sw_f[warp] = xi.f;
+    }
+    __syncthreads();
+    Seg carry{S.tc_c, S.tc_s, S.tc_mn, S.tc_mx, S.tc_f};
+    for (int w = 0; w < (int)warp; ++w) carry = seg_combine(carry, Seg{S.sw_c[w], S.sw_s[w], S.sw_mn[w], S.sw_mx[w], S.sw_f[w]});
+    Seg acc = seg_combine(carry, ex);
+    unsigned long long hidx = base + tile_heads + head_off;  // heads up to and including the current row
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!valid[j]) break;
+      acc = seg_combine(acc, Seg{1ull, (unsigned long long)v[j], v[j], v[j], head[j] ? 1u : 0u});
+      hidx += head[j];
+      if (!last[j]) continue;
+      if (acc.f) {  // the segment's head lies in this block: its row is complete here
+        const unsigned long long pos = hidx - 1;
+        if (pos < P.o_cap) {
+          P.o_keys[pos] = k[j];
+          if (P.o_count) P.o_count[pos] = acc.c;
+          if (P.o_sum) P.o_sum[pos] = (long long)acc.s;
+          if (P.o_min) P.o_min[pos] = acc.mn;
+          if (P.o_max) P.o_max[pos] = acc.mx;
+        } else {
+          set_status(C, AGG_ERR_OUTPUT_CAPACITY);
+        }
+      } else {  // continues a segment of an earlier block
+        S.lead_c = acc.c;
+        S.lead_s = acc.s;
+        S.lead_mn = acc.mn;
+        S.lead_mx = acc.mx;
+        S.lead_valid = 1;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // carry into the next tile: everything of this block so far
+      for (int w = 0; w < WARPS; ++w) carry = seg_combine(carry, Seg{S.sw_c[w], S.sw_s[w], S.sw_mn[w], S.sw_mx[w], S.sw_f[w]});
+      S.tc_c = carry.c;
+      S.tc_s = carry.s;
+      S.tc_mn = carry.mn;
+      S.tc_mx = carry.mx;
+      S.tc_f = carry.f;
+    }
+    tile_heads += tile_total;
+    __syncthreads();
+  }
+
+  // ---- S4: leading partials into the rows of segments that began earlier
+  if (!grid_barrier(T, C, P.timeout_ns, S)) return -1;
+  if (threadIdx.x == 0 && S.lead_valid && base > 0) {
+    const unsigned long long pos = base - 1;
+    if (pos < P.o_cap) {
+      if (P.o_count) atomicAdd(reinterpret_cast<unsigned long long*>(P.o_count + pos), S.lead_c);
+      if (P.o_sum) atomicAdd(reinterpret_cast<unsigned long long*>(P.o_sum + pos), S.lead_s);
+      if (P.o_min) atomicMin(reinterpret_cast<long long*>(P.o_min + pos), S.lead_mn);
+      if (P.o_max) atomicMax(reinterpret_cast<long long*>(P.o_max + pos), S.lead_mx);
+    }
+  }
+  if (T.bid == 0 && threadIdx.x == 0) {
+    C->out_count = n_groups;
+    C->resident_groups[0] = n_groups;
+    C->sorted_used = 1;
+  }
+  return 1;
+}
 
 // ---------------------------------------------------------------- the kernel
 
@@ -1619,6 +1912,18 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
   Smem& S = *reinterpret_cast<Smem*>(smem_raw);
   const Cache cc = carve_cache(smem_raw + ((sizeof(Smem) + 15) & ~size_t(15)), P.ns, Ent<ENT>::MM);
   const Team T{gridDim.x, blockIdx.x};
+  // sorted input: one segmented reduction, no table (falls through when unsorted)
+  if (P.sorted_probe && P.n >= 2 && sorted_sample(P, S)) {
+    Timer total;
+    total.start(T);
+    const int r = sorted_groupby<ENT, VT>(P, T, S);
+    if (r < 0) return;
+    if (r > 0) {
+      total.lap(T, P.ctrl, PH_TOTAL);
+      final_step(P, T, 1);
+      return;
+    }
+  }
   run_groupby<ENT, VT>(P, T, S, cc);
 }
 
@@ -1856,6 +2161,7 @@ __global__ void __launch_bounds__(EMIT_THREADS) fast_emit_kernel(const HashParam
     C->last_resident_groups[l] = l == 0 ? ng : 0;
   }
   for (int ph = 0; ph < PHASES; ++ph) C->last_phase_ns[ph] = 0;
+  C->last_sorted = 0;
   C->out_count = 0;
   __threadfence();
   C->done_count = 0;
@@ -2146,6 +2452,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     C->resident_groups[l] = 0;
   }
   for (int ph = 0; ph < PHASES; ++ph) C->last_phase_ns[ph] = 0;
+  C->last_sorted = 0;
   C->overflow_used[0] = 0;
   C->overflow_used[1] = 0;
   C->out_count = 0;

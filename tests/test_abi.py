@@ -105,3 +105,5 @@ def test_plan_picks_the_in_budget_paths(lib):
     assert gb.plan(64 << 20, 1000, gb.make_spec(ops=15, path=_abi.AGG_PATH_SORT))["in_budget_path"] == 0
     with pytest.raises(_abi.AggError):
         gb.plan(64 << 20, 10, spec, _abi.agg_tuning(in_budget=3))
+    with pytest.raises(_abi.AggError):
+        gb.plan(64 << 20, 10, spec, _abi.agg_tuning(sorted_input=3))
