@@ -99,6 +99,12 @@ typedef struct agg_tuning {
                               data): a sampled order check, then one segmented reduction with no
                               table when the keys are non-decreasing.  0 = default (on), 2 = off.
                               Results do not depend on it */
+  uint32_t max_levels;     /* recursion depth cap: records that reach this level are sorted and
+                              reduced inside the run instead of partitioned again (Section 4.3's
+                              fallback).  0 = default (the levels a sort-based split of 64-bit keys
+                              by the fan-out's bits would need, at most AGG_MAX_LEVELS - 1), else
+                              1..AGG_MAX_LEVELS - 1.  Results do not depend on it */
+  uint32_t reserved;       /* must be 0 */
 } agg_tuning;
 
 /* Output arrays, device pointers owned by the caller, one row per group.
@@ -139,6 +145,8 @@ typedef struct agg_stats {
                                                     aggregation, barrier waits, round emit, total,
                                                     shared-memory rounds: count, scatter, aggregate */
   uint64_t sorted_input;                         /* 1 when the run took the sorted-input path */
+  uint64_t fallback_records;                     /* records the recursion fallback sorted (0 = none) */
+  uint64_t fallback_level;                       /* the level at which it ran */
 } agg_stats;
 
 /* Planner output (host-only arithmetic, no GPU needed). */

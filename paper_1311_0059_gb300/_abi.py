@@ -42,7 +42,8 @@ class agg_spec(ctypes.Structure):
 class agg_tuning(ctypes.Structure):
     _fields_ = [("max_load_factor", ctypes.c_double), ("smem_entries", ctypes.c_uint32),
                 ("fan_out", ctypes.c_uint32), ("warp_dedup", ctypes.c_uint32), ("wait_limit_us", ctypes.c_uint32),
-                ("fudge", ctypes.c_double), ("in_budget", ctypes.c_uint32), ("sorted_input", ctypes.c_uint32)]
+                ("fudge", ctypes.c_double), ("in_budget", ctypes.c_uint32), ("sorted_input", ctypes.c_uint32),
+                ("max_levels", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class agg_output(ctypes.Structure):
@@ -56,7 +57,8 @@ class agg_stats(ctypes.Structure):
                 ("spill_bytes_written", _U64), ("spill_bytes_read", _U64), ("rows_at_full", _U64),
                 ("table_slots", _U64), ("table_capacity", _U64), ("table_bytes", _U64), ("budget_bytes", _U64),
                 ("staging_bytes", _U64), ("fan_out", _U64), ("status_bits", _U64), ("kernel_launches", _U64),
-                ("phase_ns", _U64 * 12), ("sorted_input", _U64)]
+                ("phase_ns", _U64 * 12), ("sorted_input", _U64), ("fallback_records", _U64),
+                ("fallback_level", _U64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

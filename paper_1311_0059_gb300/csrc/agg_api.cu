@@ -104,6 +104,7 @@ agg_tuning effective(const agg_tuning* t) {
   e.wait_limit_us = t ? t->wait_limit_us : 0;
   e.in_budget = (t && t->in_budget) ? t->in_budget : 1;  // on unless asked off
   e.sorted_input = (t && t->sorted_input) ? t->sorted_input : 1;
+  e.max_levels = t ? t->max_levels : 0;
   return e;
 }
 
@@ -117,7 +118,8 @@ bool valid_tuning(const agg_tuning* t) {
   if (t->warp_dedup > 2) return false;
   if (t->wait_limit_us > MAX_WAIT_LIMIT_US) return false;
   if (t->fudge < 0 || t->fudge > 16) return false;
-  if (t->in_budget > 2 || t->sorted_input > 2) return false;
+  if (t->in_budget > 2 || t->sorted_input > 2 || t->reserved != 0) return false;
+  if (t->max_levels >= AGG_MAX_LEVELS) return false;
   return true;
 }
 
@@ -524,6 +526,8 @@ agg_status hash_enqueue(agg_handle* h, const int64_t* d_keys, const void* d_vals
   p.cache = h->tune.smem_entries != 1;
   p.dedup = h->tune.warp_dedup == 1 ? 1 : 0;
   p.no_prefetch = host_input ? 1 : 0;
+  hash_fallback_plan(fan, h->tune.max_levels, (uint32_t)h->ki.blocks, h->slots, h->es, p.ns, h->stg_mem[0] != nullptr,
+                     &p);
   // the sorted-input path combines block boundaries with atomics on the output
   // rows: device outputs only
   p.sorted_probe = !host_input && h->tune.sorted_input != 2 && h->ki.blocks <= MAX_GRID ? 1 : 0;
@@ -665,6 +669,8 @@ agg_status agg_get_stats(agg_handle* h, agg_stats* s) {
   s->status_bits = c.status_bits;
   s->kernel_launches = h->launches + sort_launches(h->sort);
   s->sorted_input = c.last_sorted;
+  s->fallback_records = c.last_fallback_records;
+  s->fallback_level = c.last_fallback_level;
   if (h->spec.path == AGG_PATH_SORT) sort_fill_stats(h->sort, s);
   return AGG_OK;
 }
@@ -998,6 +1004,7 @@ agg_status agg_batch_create(const agg_spec* spec, const agg_batch_item* items, u
       p.cache = 1;
       p.dedup = tune.warp_dedup == 1 ? 1 : 0;
       p.timeout_ns = TIMEOUT_NS;
+      hash_fallback_plan((uint32_t)plan[i].fan, 0, b->team_blocks, plan[i].slots, b->es, p.ns, p.stg[0] != nullptr, &p);
     }
   }
   std::vector<uint32_t> toff(b->nteams + 1, 0), titems;
@@ -1185,13 +1192,13 @@ void pool_free(RangePool& p, uint64_t off, uint64_t len) {
   }
 }
 
-// Thread blocks a query would like: about 64k rows per block, a power of two
-// from 8 to the whole GPU.  A server that runs one query at a time gives each
-// query the whole GPU.
+// Thread blocks a query would like: about 8k rows per block (four tiles), a
+// power of two from 8 to the whole GPU.  A server that runs one query at a
+// time gives each query the whole GPU.
 uint32_t team_wanted(uint64_t n, uint32_t all_blocks, uint32_t max_active) {
   if (max_active == 1) return all_blocks;
   uint32_t b = 8;
-  while (b < all_blocks && (uint64_t)b * 65536 < n) b <<= 1;
+  while (b < all_blocks && (uint64_t)b * 8192 < n) b <<= 1;
   return std::min(b, all_blocks);
 }
 
@@ -1207,6 +1214,9 @@ struct QueryPlan {
   uint64_t slots = 0, chunks = 0, data = 0, meta = 0, stg_len = 0;
   uint32_t fan = 16, team = 0;
   bool may_spill = false;
+  int in_budget = 0;      // 1 partitioned, 2 single table (ordinary launches, no team), 0 the spilling kernel
+  PartPlan pp;
+  uint32_t s_fast = 0;
 };
 
 // Table size, fan-out and staging of a query run by `team` blocks.
@@ -1222,6 +1232,18 @@ QueryPlan plan_query(const agg_server* s, const agg_query& q, uint32_t team) {
   si.expected_groups = q.expected_groups;
   P.fan = plan_fan(&si, s->tune, n, q.budget, s->es);
   P.team = team;
+  // every group fits the table at once: the in-budget paths, no staging
+  const uint32_t ns = s->tune.smem_entries;
+  if (hash_part_plan(n, P.slots, s->es, ns, &P.pp)) {
+    P.in_budget = 1;
+  } else if ((P.s_fast = hash_fast_slots(n, P.slots)) != 0) {
+    P.in_budget = 2;
+  }
+  if (P.in_budget) {
+    P.team = 0;
+    P.may_spill = false;
+    return P;
+  }
   if (P.may_spill) {
     P.chunks = (n + CH - 1) / CH + (uint64_t)team * P.fan + 8;
     P.data = align_up(P.chunks * CH * REC_BYTES, 256);
@@ -1243,8 +1265,10 @@ agg_status server_launch(agg_server* s, ServerQuery& sq, const QueryPlan& P, int
   uint8_t* ent = base + P.L.ent_off;
   const uint64_t n = q.n;
   if (q.ready && cudaStreamWaitEvent(st, static_cast<cudaEvent_t>(q.ready), 0) != cudaSuccess) return AGG_ERR_CUDA;
+  // the entries this run uses (and the side slot after them) start empty
+  const uint32_t used = P.in_budget == 1 ? P.pp.s_ovf : P.in_budget == 2 ? P.s_fast : (uint32_t)P.slots;
   if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st) != cudaSuccess ||
-      hash_init_table(ent, tags, (uint32_t)P.slots, s->ent_kind, st) != cudaSuccess)
+      hash_init_table(ent, tags, used, s->ent_kind, st) != cudaSuccess)
     return AGG_ERR_CUDA;
   s->launches += 1;
   if (s->inject_fail_at && s->launches == s->inject_fail_at) return AGG_ERR_CUDA;  // host-injected failure
@@ -1274,7 +1298,7 @@ agg_status server_launch(agg_server* s, ServerQuery& sq, const QueryPlan& P, int
   p.ctrl = ctrl;
   p.ent = ent;
   p.tags = tags;
-  p.slots = (uint32_t)P.slots;
+  p.slots = used;  // the side slot follows the entries in use
   p.seed = s->spec.seed;
   p.ops = s->spec.ops;
   p.fan_log2 = log2u(P.fan);
@@ -1284,9 +1308,21 @@ agg_status server_launch(agg_server* s, ServerQuery& sq, const QueryPlan& P, int
   p.cache = 1;
   p.dedup = s->tune.warp_dedup == 1 ? 1 : 0;
   p.timeout_ns = TIMEOUT_NS;
-  KernelInfo ki = s->ki;
-  ki.blocks = (int)P.team;
-  if (hash_launch(s->ent_kind, s->spec.value_type, p, ki, st) != cudaSuccess) return AGG_ERR_CUDA;
+  if (P.in_budget == 1) {
+    // the scratch of the partitions lies above the overflow table and its side slot
+    p.s_act0 = P.pp.s_ovf;
+    if (hash_part_launch(s->ent_kind, s->spec.value_type, p, P.pp, s->es, s->ki.smem, st) != cudaSuccess)
+      return AGG_ERR_CUDA;
+  } else if (P.in_budget == 2) {
+    p.s_act0 = P.s_fast;
+    if (hash_fast_launch(s->ent_kind, s->spec.value_type, p, P.s_fast, s->ki.smem, st) != cudaSuccess)
+      return AGG_ERR_CUDA;
+  } else {
+    hash_fallback_plan(P.fan, 0, P.team, P.slots, s->es, p.ns, p.stg[0] != nullptr, &p);
+    KernelInfo ki = s->ki;
+    ki.blocks = (int)P.team;
+    if (hash_launch(s->ent_kind, s->spec.value_type, p, ki, st) != cudaSuccess) return AGG_ERR_CUDA;
+  }
   if (cudaMemcpyAsync(s->pinned + 2 * slot, &ctrl->status_bits, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaMemcpyAsync(s->pinned + 2 * slot + 1, &ctrl->last_n_groups, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaEventRecord(s->events[slot], st) != cudaSuccess)
@@ -1436,12 +1472,15 @@ agg_status agg_server_progress(agg_server* s, uint32_t* completed) {
     if (slot < 0) break;
     const uint64_t t = *it;
     ServerQuery& sq = s->queries[t];
-    const uint32_t want = team_wanted(sq.q.n, all, (uint32_t)s->slot_ticket.size());
+    // A query that fits its table at once runs on the in-budget kernels:
+    // ordinary launches that wait on nothing and hold no team.
+    const bool in_budget = plan_query(s, sq.q, 0).in_budget != 0;
+    const uint32_t want = in_budget ? 0u : team_wanted(sq.q.n, all, (uint32_t)s->slot_ticket.size());
     const bool big = want > SMALL_TEAM && s->slot_ticket.size() > 1;
     uint32_t avail = all - s->blocks_in_use;
     if (big) avail = std::min(avail, big_cap - std::min(big_cap, s->big_blocks_in_use));
     const uint32_t team = std::min(want, avail);
-    if ((big && big_blocked) || team < std::min(want, 8u)) {
+    if (!in_budget && ((big && big_blocked) || team < std::min(want, 8u))) {
       if (big) big_blocked = true;
       ++it;
       continue;
@@ -1458,9 +1497,9 @@ agg_status agg_server_progress(agg_server* s, uint32_t* completed) {
     sq.pool_len = P.L.total;
     sq.stg_off = soff;
     sq.stg_len = P.stg_len;
-    sq.team = team;
-    s->blocks_in_use += team;
-    if (team > SMALL_TEAM) s->big_blocks_in_use += team;
+    sq.team = P.team;
+    s->blocks_in_use += P.team;
+    if (P.team > SMALL_TEAM) s->big_blocks_in_use += P.team;
     sq.slot = slot;
     const agg_status st = server_launch(s, sq, P, slot);
     sq.info.t_start = s->now();

@@ -77,6 +77,10 @@ struct alignas(128) Ctrl {
   unsigned int sorted_fail;               // sorted-input path: a key below its predecessor was found
   unsigned int sorted_used;               // sorted-input path: this run completed on it
   unsigned long long sorted_heads[MAX_GRID];  // sorted-input path: segment heads in each block's rows
+  unsigned int fallback_now;              // this level's records go to the sort fallback
+  unsigned int pad_fb;
+  unsigned long long fallback_records;    // records aggregated by the sort fallback
+  unsigned long long fallback_level;      // level at which it ran (0 = none)
   // ---- snapshot of the last completed run
   unsigned long long last_n_rows;
   unsigned long long last_n_groups;
@@ -87,6 +91,8 @@ struct alignas(128) Ctrl {
   unsigned long long last_spill_records[AGG_MAX_LEVELS];
   unsigned long long last_resident_groups[AGG_MAX_LEVELS];
   unsigned long long last_sorted;         // 1 when the last run took the sorted-input path
+  unsigned long long last_fallback_records;
+  unsigned long long last_fallback_level;
 };
 
 // Everything one hash-path kernel launch needs (passed by value).
@@ -122,6 +128,8 @@ struct HashParams {
   uint32_t cache;      // shared-memory cache of resident groups on/off
   uint32_t no_prefetch;  // input in host memory: no bulk L2 prefetch of input tiles
   uint32_t sorted_probe; // try the sorted-input path first (a sampled order check decides)
+  uint32_t max_levels;   // records reaching this level go to the sort fallback
+  uint32_t fallback_ok;  // the sort fallback has its shared memory and scratch (else the depth cap is an error)
   uint64_t timeout_ns; // bounded waits give up after this long
 };
 
@@ -131,6 +139,11 @@ struct KernelInfo {
 };
 
 // hash_path.cu
+// Depth cap and availability of the sort fallback for a run of `blocks` blocks
+// over `slots` table slots of `es` bytes with `ns` shared-memory entries
+// (`max_levels` 0 = default: the levels a sort-based algorithm would need).
+void hash_fallback_plan(uint32_t fan, uint32_t max_levels, uint32_t blocks, uint64_t slots, uint32_t es, uint32_t ns,
+                        bool staging, HashParams* p);
 cudaError_t hash_kernel_info(int ent_kind, int vt, uint32_t ns, int device, KernelInfo* out);
 cudaError_t hash_launch(int ent_kind, int vt, const HashParams& p, const KernelInfo& ki, cudaStream_t s);
 cudaError_t hash_init_table(uint8_t* ent, uint32_t* tags, uint32_t slots, int ent_kind, cudaStream_t s);

@@ -1316,6 +1316,11 @@ __device__ void final_step(const HashParams& P, const Team& T, uint32_t levels) 
   C->last_sorted = V->sorted_used;
   C->sorted_used = 0;
   C->sorted_fail = 0;
+  C->last_fallback_records = V->fallback_records;
+  C->last_fallback_level = V->fallback_level;
+  C->fallback_records = 0;
+  C->fallback_level = 0;
+  C->fallback_now = 0;
   C->occupancy = 0;
   C->out_count = 0;
   C->pool_next[0] = 0;
@@ -1391,71 +1396,103 @@ __device__ __noinline__ bool sorted_sample(const HashParams& P, Smem& S) {
   return __syncthreads_and(ok) != 0;
 }
 
+// Row sources of the segmented reduction: the caller's input (keys and
+// values of type VT), or records (key, int64 value) of a contiguous buffer.
 template <int VT>
-__device__ __forceinline__ void sorted_load(const HashParams& P, uint64_t row, uint64_t r1, long long (&k)[4],
-                                            long long (&v)[4], bool with_vals) {
-  if (P.vec_ok && row + 3 < r1) {
-    const longlong2 k01 = __ldcs(reinterpret_cast<const longlong2*>(P.keys + row));
-    const longlong2 k23 = __ldcs(reinterpret_cast<const longlong2*>(P.keys + row + 2));
-    k[0] = k01.x;
-    k[1] = k01.y;
-    k[2] = k23.x;
-    k[3] = k23.y;
-    if (!with_vals || !P.has_vals) {
-      v[0] = v[1] = v[2] = v[3] = 0;
-    } else if (VT == AGG_I64) {
-      const longlong2 v01 = __ldcs(reinterpret_cast<const longlong2*>(static_cast<const long long*>(P.vals) + row));
-      const longlong2 v23 = __ldcs(reinterpret_cast<const longlong2*>(static_cast<const long long*>(P.vals) + row + 2));
-      v[0] = v01.x;
-      v[1] = v01.y;
-      v[2] = v23.x;
-      v[3] = v23.y;
-    } else {
-      const int2 v01 = __ldcs(reinterpret_cast<const int2*>(static_cast<const int*>(P.vals) + row));
-      const int2 v23 = __ldcs(reinterpret_cast<const int2*>(static_cast<const int*>(P.vals) + row + 2));
-      v[0] = v01.x;
-      v[1] = v01.y;
-      v[2] = v23.x;
-      v[3] = v23.y;
+struct InputRows {
+  const HashParams& P;
+  __device__ long long key(uint64_t i) const { return __ldcg(P.keys + i); }
+  __device__ __forceinline__ void load4(uint64_t row, uint64_t r1, long long (&k)[4], long long (&v)[4],
+                                        bool with_vals) const {
+    if (P.vec_ok && row + 3 < r1) {
+      const longlong2 k01 = __ldcs(reinterpret_cast<const longlong2*>(P.keys + row));
+      const longlong2 k23 = __ldcs(reinterpret_cast<const longlong2*>(P.keys + row + 2));
+      k[0] = k01.x;
+      k[1] = k01.y;
+      k[2] = k23.x;
+      k[3] = k23.y;
+      if (!with_vals || !P.has_vals) {
+        v[0] = v[1] = v[2] = v[3] = 0;
+      } else if (VT == AGG_I64) {
+        const longlong2 v01 = __ldcs(reinterpret_cast<const longlong2*>(static_cast<const long long*>(P.vals) + row));
+        const longlong2 v23 =
+            __ldcs(reinterpret_cast<const longlong2*>(static_cast<const long long*>(P.vals) + row + 2));
+        v[0] = v01.x;
+        v[1] = v01.y;
+        v[2] = v23.x;
+        v[3] = v23.y;
+      } else {
+        const int2 v01 = __ldcs(reinterpret_cast<const int2*>(static_cast<const int*>(P.vals) + row));
+        const int2 v23 = __ldcs(reinterpret_cast<const int2*>(static_cast<const int*>(P.vals) + row + 2));
+        v[0] = v01.x;
+        v[1] = v01.y;
+        v[2] = v23.x;
+        v[3] = v23.y;
+      }
+      return;
     }
-    return;
-  }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    k[j] = 0;
-    v[j] = 0;
-    if (row + j < r1) {
-      k[j] = __ldcs(P.keys + row + j);
-      if (with_vals && P.has_vals)
-        v[j] = VT == AGG_I64 ? __ldcs(static_cast<const long long*>(P.vals) + row + j)
-                             : (long long)__ldcs(static_cast<const int*>(P.vals) + row + j);
+    for (int j = 0; j < 4; ++j) {
+      k[j] = 0;
+      v[j] = 0;
+      if (row + j < r1) {
+        k[j] = __ldcs(P.keys + row + j);
+        if (with_vals && P.has_vals)
+          v[j] = VT == AGG_I64 ? __ldcs(static_cast<const long long*>(P.vals) + row + j)
+                               : (long long)__ldcs(static_cast<const int*>(P.vals) + row + j);
+      }
     }
   }
-}
+  __device__ void prefetch(uint64_t row, uint64_t rows, bool with_vals) const {
+    prefetch_l2(P.keys + row, (uint32_t)(rows * 8));
+    if (with_vals && P.has_vals)
+      prefetch_l2(static_cast<const char*>(P.vals) + row * (VT == AGG_I64 ? 8 : 4), (uint32_t)(rows * (VT == AGG_I64 ? 8 : 4)));
+  }
+};
 
-// Returns 1 when the run completed on the sorted path, 0 when the input is
-// not sorted (nothing was written; the hash path must run), -1 when a bounded
-// wait gave up.
-template <int ENT, int VT>
-__device__ __noinline__ int sorted_groupby(const HashParams& P, const Team& T, Smem& S) {
+struct RecordRows {
+  const longlong2* rec;
+  __device__ long long key(uint64_t i) const { return __ldcg(&rec[i].x); }
+  __device__ __forceinline__ void load4(uint64_t row, uint64_t r1, long long (&k)[4], long long (&v)[4], bool) const {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      k[j] = 0;
+      v[j] = 0;
+      if (row + j < r1) {
+        const longlong2 x = __ldcs(rec + row + j);
+        k[j] = x.x;
+        v[j] = x.y;
+      }
+    }
+  }
+  __device__ void prefetch(uint64_t row, uint64_t rows, bool) const { prefetch_l2(rec + row, (uint32_t)(rows * 16)); }
+};
+
+// Segmented reduction of n rows in non-decreasing key order (checked when
+// check_order is set: a descent makes it return 0 after a grid barrier, with
+// nothing written).  Groups go to the output rows out_base + head rank.
+// Returns 1 when done (every block gets the group count in *groups), -1 when
+// a bounded wait gave up.
+template <class Rows>
+__device__ __noinline__ int seg_reduce(const HashParams& P, const Team& T, Smem& S, const Rows& src, uint64_t n,
+                                       bool check_order, unsigned long long out_base, unsigned long long* groups) {
   Ctrl* C = P.ctrl;
-  const uint64_t n = P.n;
   const uint64_t per = (((n + T.nb - 1) / T.nb) + 3) & ~3ull;  // rows per block, a multiple of 4
   const uint64_t r0 = (uint64_t)T.bid * per < n ? (uint64_t)T.bid * per : n;
   const uint64_t r1 = r0 + per < n ? r0 + per : n;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  // ---- S1: order check and segment heads of this block's rows
+  // ---- S1: segment heads of this block's rows (and the order check)
   uint32_t heads = 0;
   bool bad = false;
   for (uint64_t t0 = r0; t0 < r1; t0 += TILE) {
     if (threadIdx.x == 0 && t0 + TILE < r1)
-      prefetch_l2(P.keys + t0 + TILE, (uint32_t)((r1 - t0 - TILE < (uint64_t)TILE ? r1 - t0 - TILE : TILE) * 8));
+      src.prefetch(t0 + TILE, r1 - t0 - TILE < (uint64_t)TILE ? r1 - t0 - TILE : TILE, false);
     const uint64_t row = t0 + 4ull * threadIdx.x;
     if (row >= r1) continue;
     long long k[4], v[4];
-    sorted_load<VT>(P, row, r1, k, v, false);
-    long long prev = row > 0 ? __ldcg(P.keys + row - 1) : 0;
+    src.load4(row, r1, k, v, false);
+    long long prev = row > 0 ? src.key(row - 1) : 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (row + j >= r1) break;
@@ -1466,13 +1503,13 @@ __device__ __noinline__ int sorted_groupby(const HashParams& P, const Team& T, S
   }
   uint32_t total;
   block_exclusive_scan(heads, total, S);
-  bad = __syncthreads_or(bad);
+  bad = __syncthreads_or(check_order && bad);
   if (threadIdx.x == 0) {
     C->sorted_heads[T.bid] = total;
     if (bad) atomicOr(&C->sorted_fail, 1u);
   }
   if (!grid_barrier(T, C, P.timeout_ns, S)) return -1;
-  if (ld_acquire_u32(&C->sorted_fail)) return 0;
+  if (check_order && ld_acquire_u32(&C->sorted_fail)) return 0;
 
   // ---- S2: rows of the output before this block's range
   unsigned long long before = 0, all = 0;
@@ -1508,19 +1545,14 @@ __device__ __noinline__ int sorted_groupby(const HashParams& P, const Team& T, S
   // ---- S3: segmented reduction, tile by tile
   unsigned long long tile_heads = 0;  // heads of this block before the current tile
   for (uint64_t t0 = r0; t0 < r1; t0 += TILE) {
-    if (threadIdx.x == 0 && t0 + TILE < r1) {
-      const uint64_t nr = r1 - t0 - TILE < (uint64_t)TILE ? r1 - t0 - TILE : TILE;
-      prefetch_l2(P.keys + t0 + TILE, (uint32_t)(nr * 8));
-      if (P.has_vals)
-        prefetch_l2(static_cast<const char*>(P.vals) + (t0 + TILE) * (VT == AGG_I64 ? 8 : 4),
-                    (uint32_t)(nr * (VT == AGG_I64 ? 8 : 4)));
-    }
+    if (threadIdx.x == 0 && t0 + TILE < r1)
+      src.prefetch(t0 + TILE, r1 - t0 - TILE < (uint64_t)TILE ? r1 - t0 - TILE : TILE, true);
     const uint64_t row = t0 + 4ull * threadIdx.x;
     long long k[4] = {0, 0, 0, 0}, v[4] = {0, 0, 0, 0};
     bool valid[4], head[4], last[4];
-    if (row < r1) sorted_load<VT>(P, row, r1, k, v, true);
-    const long long prev = row > 0 && row < r1 ? __ldcg(P.keys + row - 1) : 0;
-    const long long next = row + 4 < n ? __ldcg(P.keys + row + 4) : 0;
+    if (row < r1) src.load4(row, r1, k, v, true);
+    const long long prev = row > 0 && row < r1 ? src.key(row - 1) : 0;
+    const long long next = row + 4 < n ? src.key(row + 4) : 0;
     uint32_t my_heads = 0;
     Seg x = seg_identity();
 #pragma unroll
@@ -1552,7 +1584,8 @@ __device__ __noinline__ int sorted_groupby(const HashParams& P, const Team& T, S
     }
     __syncthreads();
     Seg carry{S.tc_c, S.tc_s, S.tc_mn, S.tc_mx, S.tc_f};
-    for (int w = 0; w < (int)warp; ++w) carry = seg_combine(carry, Seg{S.sw_c[w], S.sw_s[w], S.sw_mn[w], S.sw_mx[w], S.sw_f[w]});
+    for (int w = 0; w < (int)warp; ++w)
+      carry = seg_combine(carry, Seg{S.sw_c[w], S.sw_s[w], S.sw_mn[w], S.sw_mx[w], S.sw_f[w]});
     Seg acc = seg_combine(carry, ex);
     unsigned long long hidx = base + tile_heads + head_off;  // heads up to and including the current row
 #pragma unroll
@@ -1562,7 +1595,7 @@ __device__ __noinline__ int sorted_groupby(const HashParams& P, const Team& T, S
       hidx += head[j];
       if (!last[j]) continue;
       if (acc.f) {  // the segment's head lies in this block: its row is complete here
-        const unsigned long long pos = hidx - 1;
+        const unsigned long long pos = out_base + hidx - 1;
         if (pos < P.o_cap) {
           P.o_keys[pos] = k[j];
           if (P.o_count) P.o_count[pos] = acc.c;
@@ -1582,7 +1615,8 @@ __device__ __noinline__ int sorted_groupby(const HashParams& P, const Team& T, S
     }
     __syncthreads();
     if (threadIdx.x == 0) {  // carry into the next tile: everything of this block so far
-      for (int w = 0; w < WARPS; ++w) carry = seg_combine(carry, Seg{S.sw_c[w], S.sw_s[w], S.sw_mn[w], S.sw_mx[w], S.sw_f[w]});
+      for (int w = 0; w < WARPS; ++w)
+        carry = seg_combine(carry, Seg{S.sw_c[w], S.sw_s[w], S.sw_mn[w], S.sw_mx[w], S.sw_f[w]});
       S.tc_c = carry.c;
       S.tc_s = carry.s;
       S.tc_mn = carry.mn;
@@ -1596,7 +1630,7 @@ __device__ __noinline__ int sorted_groupby(const HashParams& P, const Team& T, S
   // ---- S4: leading partials into the rows of segments that began earlier
   if (!grid_barrier(T, C, P.timeout_ns, S)) return -1;
   if (threadIdx.x == 0 && S.lead_valid && base > 0) {
-    const unsigned long long pos = base - 1;
+    const unsigned long long pos = out_base + base - 1;
     if (pos < P.o_cap) {
       if (P.o_count) atomicAdd(reinterpret_cast<unsigned long long*>(P.o_count + pos), S.lead_c);
       if (P.o_sum) atomicAdd(reinterpret_cast<unsigned long long*>(P.o_sum + pos), S.lead_s);
@@ -1604,12 +1638,148 @@ __device__ __noinline__ int sorted_groupby(const HashParams& P, const Team& T, S
       if (P.o_max) atomicMax(reinterpret_cast<long long*>(P.o_max + pos), S.lead_mx);
     }
   }
-  if (T.bid == 0 && threadIdx.x == 0) {
-    C->out_count = n_groups;
-    C->resident_groups[0] = n_groups;
-    C->sorted_used = 1;
-  }
+  *groups = n_groups;
   return 1;
+}
+
+// The sorted-input path over the caller's rows: 1 done, 0 not sorted (the
+// hash path must run), -1 a bounded wait gave up.
+template <int ENT, int VT>
+__device__ int sorted_groupby(const HashParams& P, const Team& T, Smem& S) {
+  unsigned long long ng = 0;
+  const int r = seg_reduce(P, T, S, InputRows<VT>{P}, P.n, true, 0ull, &ng);
+  if (r > 0 && T.bid == 0 && threadIdx.x == 0) {
+    P.ctrl->out_count = ng;
+    P.ctrl->resident_groups[0] = ng;
+    P.ctrl->sorted_used = 1;
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------- recursion fallback (sort path)
+
+// The hybrid hash falls back to a sort-based aggregation for records that
+// partitioning no longer shrinks (Section 4.3: when the grace levels exceed
+// those a sort-based algorithm would need, or a partition's output is more
+// than 80% of its input).  Here a level falls back when it reaches the depth
+// cap, or when the records completed at the level before formed more than 0.8
+// groups per record.  All of the level's records are then sorted by key with
+// an LSD radix sort inside the kernel (eight passes of eight bits: a digit
+// histogram per block, column scans, and a stable scatter that ranks each
+// round of THREADS records by warp (__match_any_sync) and across warps), and
+// reduced by segments like sorted input.  Pass 0 reads the staging chunks; the
+// passes alternate between the two staging areas' data regions.
+
+constexpr int RADIX = 256;
+
+__device__ __forceinline__ uint32_t radix_digit(long long key, int pass) {
+  return (uint32_t)((((uint64_t)key) ^ 0x8000000000000000ull) >> (8 * pass)) & 0xFFu;
+}
+
+// Stable scatter of one round: `valid` lanes hold records in input order
+// (thread order); wcnt (WARPS x RADIX, zero on entry and exit), off (the
+// block's next free position per digit) and rtot are in shared memory.
+__device__ __forceinline__ void radix_round(bool valid, const longlong2& rec, int pass, longlong2* out, uint16_t* wcnt,
+                                            uint32_t* off, uint32_t* rtot) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t d = valid ? radix_digit(rec.x, pass) : (uint32_t)RADIX + lane;  // idle lanes match no one
+  const uint32_t peers = __match_any_sync(FULL_MASK, d);
+  const uint32_t rank = __popc(peers & lanemask_lt());
+  if (valid && rank == 0) wcnt[warp * RADIX + d] = (uint16_t)__popc(peers);
+  __syncthreads();
+  for (uint32_t dd = threadIdx.x; dd < (uint32_t)RADIX; dd += THREADS) {  // exclusive prefix over the warps
+    uint32_t run = 0;
+    for (int w = 0; w < WARPS; ++w) {
+      const uint32_t c = wcnt[w * RADIX + dd];
+      wcnt[w * RADIX + dd] = (uint16_t)run;
+      run += c;
+    }
+    rtot[dd] = run;
+  }
+  __syncthreads();
+  if (valid) out[(uint64_t)off[d] + wcnt[warp * RADIX + d] + rank] = rec;
+  __syncthreads();
+  for (uint32_t dd = threadIdx.x; dd < (uint32_t)RADIX; dd += THREADS) {
+    off[dd] += rtot[dd];
+    for (int w = 0; w < WARPS; ++w) wcnt[w * RADIX + dd] = 0;
+  }
+  __syncthreads();
+}
+
+// Sorts the R records of the chunks [0, nch) of staging area `src` by key
+// into bufB (bufA is the other buffer).  H (team blocks x RADIX) and TOT
+// (RADIX) are scratch words.  False when a bounded wait gave up.
+__device__ __noinline__ bool fallback_sort(const HashParams& P, const Team& T, Smem& S, const Cache& cc, uint32_t src,
+                                           uint64_t nch, uint64_t R, longlong2* bufA, longlong2* bufB, uint32_t* H,
+                                           uint32_t* TOT) {
+  uint16_t* wcnt = reinterpret_cast<uint16_t*>(cc.key);
+  uint32_t* off = reinterpret_cast<uint32_t*>(wcnt + WARPS * RADIX);
+  uint32_t* rtot = off + RADIX;
+  const uint32_t* dcount = P.dir_count[src];
+  const longlong2* chunks = reinterpret_cast<const longlong2*>(P.stg[src]);
+  const uint64_t c0 = nch * T.bid / T.nb, c1 = nch * (T.bid + 1) / T.nb;
+  const uint64_t a0 = R * T.bid / T.nb, a1 = R * (T.bid + 1) / T.nb;
+  for (int pass = 0; pass < 8; ++pass) {
+    const longlong2* in = (pass & 1) ? bufA : bufB;  // pass 0 reads the chunks
+    longlong2* out = (pass & 1) ? bufB : bufA;
+    // digit histogram of this block's records
+    for (uint32_t i = threadIdx.x; i < (uint32_t)RADIX; i += THREADS) off[i] = 0;
+    __syncthreads();
+    if (pass == 0) {
+      for (uint64_t c = c0; c < c1; ++c) {
+        const uint32_t cnt = __ldcg(dcount + c);
+        for (uint32_t j = threadIdx.x; j < cnt; j += THREADS)
+          sh_red_add_u32(&off[radix_digit(__ldcg(&chunks[c * CH + j].x), 0)], 1u);
+      }
+    } else {
+      for (uint64_t i = a0 + threadIdx.x; i < a1; i += THREADS) sh_red_add_u32(&off[radix_digit(__ldcg(&in[i].x), pass)], 1u);
+    }
+    __syncthreads();
+    for (uint32_t d = threadIdx.x; d < (uint32_t)RADIX; d += THREADS) __stcg(H + (size_t)T.bid * RADIX + d, off[d]);
+    if (!grid_barrier(T, P.ctrl, P.timeout_ns, S)) return false;
+    // column scans: for each digit, exclusive offsets of the blocks in order
+    for (uint32_t d = T.bid; d < (uint32_t)RADIX; d += T.nb) {
+      const uint32_t per = (T.nb + THREADS - 1) / THREADS, b0 = threadIdx.x * per;
+      uint32_t mine = 0;
+      for (uint32_t i = 0; i < per; ++i)
+        if (b0 + i < T.nb) mine += __ldcg(H + (size_t)(b0 + i) * RADIX + d);
+      uint32_t total;
+      uint32_t ex = block_exclusive_scan(mine, total, S);
+      for (uint32_t i = 0; i < per; ++i) {
+        if (b0 + i >= T.nb) break;
+        uint32_t* q = H + (size_t)(b0 + i) * RADIX + d;
+        const uint32_t x = __ldcg(q);
+        __stcg(q, ex);
+        ex += x;
+      }
+      if (threadIdx.x == 0) __stcg(TOT + d, total);
+    }
+    if (!grid_barrier(T, P.ctrl, P.timeout_ns, S)) return false;
+    // this block's first position for every digit
+    uint32_t tt;
+    const uint32_t ex = block_exclusive_scan(threadIdx.x < (uint32_t)RADIX ? __ldcg(TOT + threadIdx.x) : 0u, tt, S);
+    if (threadIdx.x < (uint32_t)RADIX) off[threadIdx.x] = ex + __ldcg(H + (size_t)T.bid * RADIX + threadIdx.x);
+    for (uint32_t i = threadIdx.x; i < (uint32_t)(WARPS * RADIX); i += THREADS) wcnt[i] = 0;
+    __syncthreads();
+    if (pass == 0) {
+      for (uint64_t c = c0; c < c1; ++c) {
+        const uint32_t cnt = __ldcg(dcount + c);
+        for (uint32_t j0 = 0; j0 < cnt; j0 += THREADS) {
+          const bool valid = j0 + threadIdx.x < cnt;
+          const longlong2 rec = valid ? __ldcg(&chunks[c * CH + j0 + threadIdx.x]) : make_longlong2(0, 0);
+          radix_round(valid, rec, 0, out, wcnt, off, rtot);
+        }
+      }
+    } else {
+      for (uint64_t i0 = a0; i0 < a1; i0 += THREADS) {
+        const bool valid = i0 + threadIdx.x < a1;
+        const longlong2 rec = valid ? __ldcg(&in[i0 + threadIdx.x]) : make_longlong2(0, 0);
+        radix_round(valid, rec, pass, out, wcnt, off, rtot);
+      }
+    }
+    if (!grid_barrier(T, P.ctrl, P.timeout_ns, S)) return false;
+  }
+  return true;
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -1758,6 +1928,26 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     // also clears the level's round counters here, before the level's first
     // barrier, so every block later reads the same values.
     if (threadIdx.x == 0 && T.bid == 0) {
+      // Does this level fall back to sorting?  Every block reads the verdict
+      // after the barrier below; the counters read here are final (the level
+      // before ended with a barrier) and are reset only after this.
+      uint32_t fb = 0;
+      if (P.fallback_ok) {
+        if (level >= P.max_levels) {
+          fb = 1;
+        } else {
+          unsigned long long rows, groups;
+          if (level == 1) {
+            rows = P.n - C->spill_records[0];
+            groups = C->resident_groups[0];
+          } else {
+            rows = C->lvl_sub_records[0] + C->lvl_sub_records[1];
+            groups = C->lvl_sub_groups[0] + C->lvl_sub_groups[1];
+          }
+          if (rows > 0 && (double)groups > 0.8 * (double)rows) fb = 1;
+        }
+      }
+      C->fallback_now = fb;
       C->pool_next[dst] = 0;
       C->overflow_used[level & 1] = 0;
       C->lvl_sub_records[0] = C->lvl_sub_records[1] = 0;
@@ -1786,6 +1976,35 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
       S.cnt[p] = 0;
     }
     if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+    if (ld_acquire_u32(&C->fallback_now)) {
+      // every record of this level: sorted by key, then reduced by segments
+      unsigned long long recs = 0;
+      for (uint32_t q = 0; q < fan; ++q) recs += __ldcg(&C->part_records[set][q]);
+      if (recs >= (1ull << 32)) {  // beyond the sort's 32-bit offsets
+        if (threadIdx.x == 0 && T.bid == 0) set_status(C, AGG_ERR_INTERNAL);
+        final_step(P, T, level + 1);
+        return true;
+      }
+      const uint32_t gsl = (P.slots / GTABLE_DIV) / BUCKET * BUCKET;
+      uint32_t* H = reinterpret_cast<uint32_t*>(P.ent + (size_t)gsl * Ent<ENT>::ES);
+      uint32_t* TOT = H + (size_t)T.nb * RADIX;
+      longlong2* bufA = reinterpret_cast<longlong2*>(P.stg[dst]);
+      longlong2* bufB = reinterpret_cast<longlong2*>(P.stg[src]);
+      if (!fallback_sort(P, T, S, cc, src, nch, recs, bufA, bufB, H, TOT)) return false;
+      const unsigned long long base = ld_relaxed_u64(&C->out_count);
+      unsigned long long ng = 0;
+      if (seg_reduce(P, T, S, RecordRows{bufB}, recs, false, base, &ng) < 0) return false;
+      if (threadIdx.x == 0 && T.bid == 0) {
+        C->out_count = base + ng;
+        C->resident_groups[level] += ng;
+        C->fallback_records = recs;
+        C->fallback_level = level;
+      }
+      restore_scratch<ENT>(P, T, gsl);
+      total.lap(T, C, PH_TOTAL);
+      final_step(P, T, level + 1);
+      return true;
+    }
     // P3: chunk lists grouped by partition
     if (threadIdx.x == 0) {
       uint32_t acc = 0;
@@ -2162,6 +2381,8 @@ __global__ void __launch_bounds__(EMIT_THREADS) fast_emit_kernel(const HashParam
   }
   for (int ph = 0; ph < PHASES; ++ph) C->last_phase_ns[ph] = 0;
   C->last_sorted = 0;
+  C->last_fallback_records = 0;
+  C->last_fallback_level = 0;
   C->out_count = 0;
   __threadfence();
   C->done_count = 0;
@@ -2453,6 +2674,8 @@ __global__ void __launch_bounds__(THREADS, 2)
   }
   for (int ph = 0; ph < PHASES; ++ph) C->last_phase_ns[ph] = 0;
   C->last_sorted = 0;
+  C->last_fallback_records = 0;
+  C->last_fallback_level = 0;
   C->overflow_used[0] = 0;
   C->overflow_used[1] = 0;
   C->out_count = 0;
@@ -2588,6 +2811,21 @@ cudaError_t hash_launch(int ent_kind, int vt, const HashParams& p, const KernelI
   void* k = pick_kernel(ent_kind, vt);
   void* args[] = {const_cast<HashParams*>(&p)};
   return cudaLaunchCooperativeKernel(k, dim3(ki.blocks), dim3(THREADS), args, ki.smem, s);
+}
+
+void hash_fallback_plan(uint32_t fan, uint32_t max_levels, uint32_t blocks, uint64_t slots, uint32_t es, uint32_t ns,
+                        bool staging, HashParams* p) {
+  uint32_t bits = 0;
+  while ((1u << bits) < fan) ++bits;
+  // the levels of log2(fan)-bit digits that a sort-based split of 64-bit keys would need
+  uint32_t cap = bits ? (64 + bits - 1) / bits : AGG_MAX_LEVELS - 1;
+  if (cap > AGG_MAX_LEVELS - 1) cap = AGG_MAX_LEVELS - 1;
+  if (max_levels) cap = max_levels;
+  p->max_levels = cap;
+  const uint64_t gslots = (slots / GTABLE_DIV) / BUCKET * BUCKET;
+  const uint64_t scratch = (slots - gslots) * es;
+  const uint64_t need = ((uint64_t)blocks * RADIX + RADIX) * 4 + 256;
+  p->fallback_ok = staging && ns >= 512 && scratch >= need && blocks <= MAX_GRID ? 1u : 0u;
 }
 
 uint32_t hash_fast_slots(uint64_t n, uint64_t slots) {

@@ -107,3 +107,15 @@ def test_plan_picks_the_in_budget_paths(lib):
         gb.plan(64 << 20, 10, spec, _abi.agg_tuning(in_budget=3))
     with pytest.raises(_abi.AggError):
         gb.plan(64 << 20, 10, spec, _abi.agg_tuning(sorted_input=3))
+
+
+def test_depth_cap_knob_is_checked_on_the_host(lib):
+    from paper_1311_0059_gb300 import groupby as gb, _abi
+    spec = gb.make_spec(ops=15, value_type=_abi.AGG_I64)
+    for ok in (0, 1, 2, 11):
+        gb.plan(64 << 20, 10, spec, _abi.agg_tuning(max_levels=ok))
+    for bad in (12, 100):
+        with pytest.raises(_abi.AggError):
+            gb.plan(64 << 20, 10, spec, _abi.agg_tuning(max_levels=bad))
+    with pytest.raises(_abi.AggError):
+        gb.plan(64 << 20, 10, spec, _abi.agg_tuning(reserved=1))

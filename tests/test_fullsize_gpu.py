@@ -131,6 +131,7 @@ def test_served_60s_stream_sampled_against_the_oracle():
     zd = [w.domain for _, w in qs if w.dist == "zipf"]
     hdev = torch.from_numpy(dg.harmonic(max(zd)).copy()).cuda()
     srv = Server(64 << 30, max_active=64, ops=15, value_type=AGG_I64)
+    gen = torch.cuda.Stream()
     live, got_results, inv = {}, {}, 0
     with pool() as p:
         pending = p.imap_unordered(oracle_workload, [(i, workload_params(qs[i][1])) for i in sorted(checked)],
@@ -160,17 +161,19 @@ def test_served_60s_stream_sampled_against_the_oracle():
                 if srv.progress():
                     for t in [t for t in live if srv.poll(t).state >= 2]:
                         finish(t)
-            k = torch.empty(w.n, dtype=torch.int64, device="cuda")
-            v = torch.empty(w.n, dtype=torch.int64, device="cuda")
-            cdf = None
-            if w.dist == "zipf":
-                cdf = hdev[:w.domain] / hdev[w.domain - 1]
-                cdf[-1] = 2.0
-            w.device(k.data_ptr(), v.data_ptr(), cdf_ptr=cdf.data_ptr() if cdf is not None else 0,
-                     stream_handle=torch.cuda.current_stream().cuda_stream)
-            torch.cuda.synchronize()
+            with torch.cuda.stream(gen):  # inputs made on a side stream; the query waits on its event
+                k = torch.empty(w.n, dtype=torch.int64, device="cuda")
+                v = torch.empty(w.n, dtype=torch.int64, device="cuda")
+                cdf = None
+                if w.dist == "zipf":
+                    cdf = hdev[:w.domain] / hdev[w.domain - 1]
+                    cdf[-1] = 2.0
+                w.device(k.data_ptr(), v.data_ptr(), cdf_ptr=cdf.data_ptr() if cdf is not None else 0,
+                         stream_handle=gen.cuda_stream)
+                ev = torch.cuda.Event()
+                ev.record(gen)
             out = Output(min(w.n, w.domain), 15, "cuda")
-            t = srv.submit(k, v, w.budget, out)
+            t = srv.submit(k, v, w.budget, out, ready_event=ev)
             live[t] = (i, k, v, out)
             if srv.progress():
                 for t in [t for t in live if srv.poll(t).state >= 2]:
