@@ -61,8 +61,17 @@ typedef enum agg_dtype { AGG_I32 = 0, AGG_I64 = 1 } agg_dtype;
 
 /* AGG_PATH_HASH: Pre-Partitioning hybrid hash (Sections 4.3, 4.3.4).
  * AGG_PATH_SORT: radix sort + segmented reduction (Section 4.1); its output is
- * in ascending signed key order. */
-typedef enum agg_path { AGG_PATH_HASH = 0, AGG_PATH_SORT = 1 } agg_path;
+ * in ascending signed key order.
+ * AGG_PATH_AUTO: each run takes the path the cost model predicts to be faster
+ * (Section 5's models in bytes, Section 7's guidance): the input and result
+ * bytes, the Pre-Partitioning spill R(1 - K/G) written and read back (Section
+ * 5.3.4), the hash path's fall back to sorting when the groups are more than
+ * 0.8 of the rows (Section 4.3), and the sort path's passes, each over a
+ * bandwidth measured for that path on GB300.  Without an expected_groups hint
+ * G is unknown and the hash path is taken.  Both paths share the handle's
+ * working memory (a sort run leaves the table to be cleared before the next
+ * hash run). */
+typedef enum agg_path { AGG_PATH_HASH = 0, AGG_PATH_SORT = 1, AGG_PATH_AUTO = 2 } agg_path;
 
 #define AGG_MIN_BUDGET ((size_t)1 << 20)
 #define AGG_MAX_LEVELS 12
@@ -104,7 +113,10 @@ typedef struct agg_tuning {
                               fallback).  0 = default (the levels a sort-based split of 64-bit keys
                               by the fan-out's bits would need, at most AGG_MAX_LEVELS - 1), else
                               1..AGG_MAX_LEVELS - 1.  Results do not depend on it */
-  uint32_t reserved;       /* must be 0 */
+  uint32_t staging_tier;   /* where the spill staging lives (outside the budget, the paper's disk):
+                              0 = default (device memory; pinned host memory, which the kernel
+                              reaches over the host link, when device memory cannot be had),
+                              1 = device memory only, 2 = host memory.  Results do not depend on it */
 } agg_tuning;
 
 /* Output arrays, device pointers owned by the caller, one row per group.
@@ -147,6 +159,8 @@ typedef struct agg_stats {
   uint64_t sorted_input;                         /* 1 when the run took the sorted-input path */
   uint64_t fallback_records;                     /* records the recursion fallback sorted (0 = none) */
   uint64_t fallback_level;                       /* the level at which it ran */
+  uint64_t staging_in_host;                      /* 1 when the staging area is in host memory */
+  uint64_t path;                                 /* path of the last run: AGG_PATH_HASH or AGG_PATH_SORT */
 } agg_stats;
 
 /* Planner output (host-only arithmetic, no GPU needed). */
@@ -162,6 +176,11 @@ typedef struct agg_plan_info {
                                partitioned into shared-memory tables (small n), 2 = in-budget, one
                                table probed linearly (n at most half the slots) */
   uint64_t partitions;      /* partitions of path 1 (else 0) */
+  double hash_bytes;        /* cost model: predicted DRAM bytes of the hash path for n rows */
+  double sort_bytes;        /* and of the sort path */
+  double hash_seconds;      /* predicted run times (bytes over each path's measured bandwidth, plus */
+  double sort_seconds;      /* its fixed launch cost) */
+  uint64_t chosen_path;     /* the path an AGG_PATH_AUTO run of n rows takes (AGG_PATH_HASH or _SORT) */
 } agg_plan_info;
 
 typedef struct agg_handle agg_handle;
@@ -295,8 +314,8 @@ typedef struct agg_query_info {
   double t_submit;      /* host steady-clock seconds */
   double t_start;       /* admitted and launched */
   double t_done;        /* completion observed by agg_server_progress */
-  uint32_t team_blocks; /* thread blocks that ran it */
-  uint32_t pad;
+  uint32_t team_blocks; /* thread blocks that ran it (0: ordinary launches, no cooperative team) */
+  uint32_t path;        /* AGG_PATH_HASH or AGG_PATH_SORT (an AGG_PATH_AUTO server chooses per query) */
 } agg_query_info;
 
 typedef struct agg_server_stats {

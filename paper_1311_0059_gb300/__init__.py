@@ -5,11 +5,11 @@ for Data Intensive Applications: A Performance Study".
 The compute path is libagg.so (hand-written CUDA for sm_103a behind the C ABI
 of include/agg.h); this package is its Python binding.
 """
-from ._abi import (AGG_COUNT, AGG_I32, AGG_I64, AGG_MAX, AGG_MIN, AGG_PATH_HASH, AGG_PATH_SORT, AGG_SUM, AggError,
-                   agg_tuning)
+from ._abi import (AGG_COUNT, AGG_I32, AGG_I64, AGG_MAX, AGG_MIN, AGG_PATH_AUTO, AGG_PATH_HASH, AGG_PATH_SORT,
+                   AGG_SUM, AggError, agg_tuning)
 
 __all__ = ["AGG_COUNT", "AGG_SUM", "AGG_MIN", "AGG_MAX", "AGG_I32", "AGG_I64", "AGG_PATH_HASH", "AGG_PATH_SORT",
-           "AggError", "agg_tuning", "GroupBy"]
+           "AGG_PATH_AUTO", "AggError", "agg_tuning", "GroupBy"]
 
 
 def __getattr__(name):

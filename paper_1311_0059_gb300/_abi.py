@@ -26,7 +26,7 @@ AGG_ERR_INTERNAL = 8
 
 AGG_COUNT, AGG_SUM, AGG_MIN, AGG_MAX = 1, 2, 4, 8
 AGG_I32, AGG_I64 = 0, 1
-AGG_PATH_HASH, AGG_PATH_SORT = 0, 1
+AGG_PATH_HASH, AGG_PATH_SORT, AGG_PATH_AUTO = 0, 1, 2
 AGG_MAX_LEVELS = 12
 AGG_MIN_BUDGET = 1 << 20
 
@@ -43,7 +43,7 @@ class agg_tuning(ctypes.Structure):
     _fields_ = [("max_load_factor", ctypes.c_double), ("smem_entries", ctypes.c_uint32),
                 ("fan_out", ctypes.c_uint32), ("warp_dedup", ctypes.c_uint32), ("wait_limit_us", ctypes.c_uint32),
                 ("fudge", ctypes.c_double), ("in_budget", ctypes.c_uint32), ("sorted_input", ctypes.c_uint32),
-                ("max_levels", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("max_levels", ctypes.c_uint32), ("staging_tier", ctypes.c_uint32)]
 
 
 class agg_output(ctypes.Structure):
@@ -58,7 +58,7 @@ class agg_stats(ctypes.Structure):
                 ("table_slots", _U64), ("table_capacity", _U64), ("table_bytes", _U64), ("budget_bytes", _U64),
                 ("staging_bytes", _U64), ("fan_out", _U64), ("status_bits", _U64), ("kernel_launches", _U64),
                 ("phase_ns", _U64 * 12), ("sorted_input", _U64), ("fallback_records", _U64),
-                ("fallback_level", _U64)]
+                ("fallback_level", _U64), ("staging_in_host", _U64), ("path", _U64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -71,7 +71,9 @@ class agg_stats(ctypes.Structure):
 class agg_plan_info(ctypes.Structure):
     _fields_ = [("entry_bytes", _U64), ("table_slots", _U64), ("table_capacity", _U64), ("fan_out", _U64),
                 ("active_slots", _U64), ("working_bytes", _U64), ("staging_bytes", _U64),
-                ("in_budget_path", _U64), ("partitions", _U64)]
+                ("in_budget_path", _U64), ("partitions", _U64), ("hash_bytes", ctypes.c_double),
+                ("sort_bytes", ctypes.c_double), ("hash_seconds", ctypes.c_double), ("sort_seconds", ctypes.c_double),
+                ("chosen_path", _U64)]
 
 
 class agg_batch_item(ctypes.Structure):
@@ -92,7 +94,7 @@ class agg_query(ctypes.Structure):
 class agg_query_info(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("n_groups", _U64), ("t_submit", ctypes.c_double),
                 ("t_start", ctypes.c_double), ("t_done", ctypes.c_double), ("team_blocks", ctypes.c_uint32),
-                ("pad", ctypes.c_uint32)]
+                ("path", ctypes.c_uint32)]
 
 
 class agg_server_stats(ctypes.Structure):

@@ -42,6 +42,7 @@ struct agg_handle {
   uint64_t reserved_rows = 0;
   uint32_t reserved_fan = 0;
   uint64_t staging_bytes = 0;
+  bool stg_host = false;  // staging areas in pinned host memory
   // device copies for agg_run_host
   void* in_buf = nullptr;
   uint64_t in_cap = 0;
@@ -56,6 +57,8 @@ struct agg_handle {
   // entries [dirty_lo, slots) hold scratch records of the partitioned in-budget
   // path (slots = none); they are restored before another run needs them
   uint64_t dirty_lo = 0;
+  bool table_dirty = false;  // AGG_PATH_AUTO: a sort run used the table's memory
+  int last_path = 0;         // path of the last run
 };
 
 namespace {
@@ -84,7 +87,7 @@ bool valid_spec(const agg_spec* s) {
   if (!s) return false;
   if (s->ops == 0 || (s->ops & ~15u)) return false;
   if (s->value_type != AGG_I32 && s->value_type != AGG_I64) return false;
-  if (s->path != AGG_PATH_HASH && s->path != AGG_PATH_SORT) return false;
+  if (s->path != AGG_PATH_HASH && s->path != AGG_PATH_SORT && s->path != AGG_PATH_AUTO) return false;
   if (s->flags != 0) return false;
   return true;
 }
@@ -105,6 +108,7 @@ agg_tuning effective(const agg_tuning* t) {
   e.in_budget = (t && t->in_budget) ? t->in_budget : 1;  // on unless asked off
   e.sorted_input = (t && t->sorted_input) ? t->sorted_input : 1;
   e.max_levels = t ? t->max_levels : 0;
+  e.staging_tier = t ? t->staging_tier : 0;
   return e;
 }
 
@@ -118,7 +122,7 @@ bool valid_tuning(const agg_tuning* t) {
   if (t->warp_dedup > 2) return false;
   if (t->wait_limit_us > MAX_WAIT_LIMIT_US) return false;
   if (t->fudge < 0 || t->fudge > 16) return false;
-  if (t->in_budget > 2 || t->sorted_input > 2 || t->reserved != 0) return false;
+  if (t->in_budget > 2 || t->sorted_input > 2 || t->staging_tier > 2) return false;
   if (t->max_levels >= AGG_MAX_LEVELS) return false;
   return true;
 }
@@ -179,6 +183,54 @@ uint32_t active_slots(uint64_t est, double lf, uint64_t slots) {
   return (uint32_t)want;
 }
 
+// ---- cost model of the two paths (Section 5's models, counted in DRAM bytes)
+//
+// Hash path: the input once; when the rows may not all fit the table
+// (n > slots / 2), the Pre-Partitioning spill R(1 - K/G) of Section 5.3.4,
+// written and read back once (the recursion completes at level 1 when its
+// partitions fit the rounds); when the groups are more than 0.8 of the rows the
+// spilled records are sorted at level 1 instead (eight radix passes, each
+// reading and writing 16-byte records, then a reduction pass); the result.
+// Sort path: a split pass when the rows exceed one round, the eight passes over
+// (key, value), a reduction pass, the result.  Times are bytes over the
+// effective bandwidth each path reached on GB300 (spilling workload: hash
+// 10.9 GB in 12.4 ms, sort about 62 GB in 38.5 ms) plus a fixed cost per run.
+constexpr double HASH_GBS = 880.0, SORT_GBS = 1620.0, INBUDGET_GBS = 300.0;
+constexpr double HASH_FIXED_S = 30e-6, SORT_FIXED_S = 120e-6;
+
+struct PathCosts {
+  double hash_bytes, sort_bytes, hash_s, sort_s;
+  int choice;  // AGG_PATH_HASH or AGG_PATH_SORT
+};
+
+PathCosts path_costs(const agg_spec* s, const agg_tuning& t, uint64_t n, size_t budget, uint32_t es,
+                     uint64_t slots) {
+  PathCosts c{};
+  const double vb = s->value_type == AGG_I64 ? 8.0 : 4.0;
+  const double rows = (double)n;
+  const double g = s->expected_groups ? std::min((double)s->expected_groups, rows) : rows;
+  const double out = g * 8.0 * (1 + __builtin_popcount(s->ops & 15u));
+  const double in = rows * (8.0 + vb);
+  const double k = t.max_load_factor * (double)slots;  // the table's planned groups (K)
+  if (n <= slots / 2) {
+    c.hash_bytes = in + out;
+    c.hash_s = c.hash_bytes / (INBUDGET_GBS * 1e9) + HASH_FIXED_S;
+  } else {
+    const double spill = g > k ? rows * (1.0 - k / g) : 0.0;  // R(1 - K/G)
+    double bytes = in + 2.0 * 16.0 * spill + out;
+    if (g > 0.8 * rows) bytes += spill * (8.0 * 32.0 + 16.0);  // level 1 sorts instead
+    c.hash_bytes = bytes;
+    c.hash_s = bytes / (HASH_GBS * 1e9) + HASH_FIXED_S;
+  }
+  const uint64_t ctrl = align_up(sizeof(Ctrl), 256);
+  const uint64_t rr = sort_rows_for(budget > ctrl ? budget - ctrl : 0);
+  c.sort_bytes = (n > rr ? 2.0 * (8.0 + vb) * rows : 0.0) + 8.0 * rows + 8.0 * 32.0 * rows + 16.0 * rows + out;
+  c.sort_s = c.sort_bytes / (SORT_GBS * 1e9) + SORT_FIXED_S;
+  // with no estimate of G the model has nothing to go on: the hash path
+  c.choice = s->expected_groups && c.sort_s < c.hash_s ? AGG_PATH_SORT : AGG_PATH_HASH;
+  return c;
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -216,7 +268,10 @@ agg_status check_device_io(uint32_t ops, int32_t value_type, const int64_t* d_ke
 
 void free_staging(agg_handle* h) {
   for (int a = 0; a < 2; ++a) {
-    if (h->stg_mem[a]) cudaFree(h->stg_mem[a]);
+    if (h->stg_mem[a]) {
+      if (h->stg_host) cudaFreeHost(h->stg_mem[a]);
+      else cudaFree(h->stg_mem[a]);
+    }
     h->stg_mem[a] = nullptr;
     h->stg[a] = nullptr;
     h->dir_part[a] = h->dir_count[a] = h->list[a] = nullptr;
@@ -225,6 +280,7 @@ void free_staging(agg_handle* h) {
   h->reserved_rows = 0;
   h->reserved_fan = 0;
   h->staging_bytes = 0;
+  h->stg_host = false;
 }
 
 agg_status reserve_staging(agg_handle* h, uint64_t rows, uint32_t fan) {
@@ -236,14 +292,38 @@ agg_status reserve_staging(agg_handle* h, uint64_t rows, uint32_t fan) {
   const uint64_t data = align_up(chunks * CH * REC_BYTES, 256);
   const uint64_t meta = align_up(chunks * 4, 256);
   const uint64_t per_area = data + 3 * meta;
-  for (int a = 0; a < 2; ++a) {
-    void* m = nullptr;
-    if (cudaMalloc(&m, per_area) != cudaSuccess) {
-      cudaGetLastError();
-      free_staging(h);
-      return AGG_ERR_OOM;
+  // device memory, or pinned host memory (mapped into the device's address
+  // space) for the host tier, or when device memory cannot be had
+  const uint32_t tier = h->tune.staging_tier;
+  bool host = tier == 2;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    bool ok = true;
+    for (int a = 0; a < 2 && ok; ++a) {
+      void* m = nullptr;
+      ok = (host ? cudaHostAlloc(&m, per_area, cudaHostAllocMapped | cudaHostAllocPortable)
+                 : cudaMalloc(&m, per_area)) == cudaSuccess;
+      if (ok) {
+        h->stg_mem[a] = m;
+        h->stg_host = host;
+      }
     }
-    h->stg_mem[a] = m;
+    if (ok) break;
+    cudaGetLastError();
+    free_staging(h);
+    if (host || tier == 1) return AGG_ERR_OOM;
+    host = true;  // the host tier
+  }
+  for (int a = 0; a < 2; ++a) {
+    void* m = h->stg_mem[a];
+    if (host) {
+      void* dp = nullptr;
+      if (cudaHostGetDevicePointer(&dp, m, 0) != cudaSuccess) {
+        cudaGetLastError();
+        free_staging(h);
+        return AGG_ERR_CUDA;
+      }
+      m = dp;
+    }
     uint8_t* b = static_cast<uint8_t*>(m);
     h->stg[a] = b;
     h->dir_part[a] = reinterpret_cast<uint32_t*>(b + data);
@@ -265,6 +345,7 @@ agg_status reinit_working(agg_handle* h, cudaStream_t s) {
   if (hash_init_table(h->ent, h->tags, (uint32_t)h->slots, h->ent_kind, s) != cudaSuccess) return AGG_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return AGG_ERR_CUDA;
   h->dirty_lo = h->slots;
+  h->table_dirty = false;
   return AGG_OK;
 }
 
@@ -316,7 +397,13 @@ agg_status agg_plan(size_t budget, const agg_spec* spec, const agg_tuning* t, ui
   out->staging_bytes = 2 * (chunks * CH * REC_BYTES + 3 * chunks * 4);
   out->in_budget_path = 0;
   out->partitions = 0;
-  if (spec->path == AGG_PATH_HASH && e.in_budget != 2) {
+  const PathCosts pc = path_costs(spec, e, n, budget, es, L.slots);
+  out->hash_bytes = pc.hash_bytes;
+  out->sort_bytes = pc.sort_bytes;
+  out->hash_seconds = pc.hash_s;
+  out->sort_seconds = pc.sort_s;
+  out->chosen_path = spec->path == AGG_PATH_AUTO ? (uint64_t)pc.choice : (uint64_t)spec->path;
+  if (spec->path != AGG_PATH_SORT && out->chosen_path == AGG_PATH_HASH && e.in_budget != 2) {
     PartPlan pp;
     if (e.smem_entries != 1 && hash_part_plan(n, L.slots, es, e.smem_entries > 1 ? e.smem_entries : DEFAULT_NS, &pp)) {
       out->in_budget_path = 1;
@@ -353,6 +440,7 @@ agg_status agg_create(size_t budget, const agg_spec* spec, agg_handle** out) {
     return AGG_ERR_BUDGET_TOO_SMALL;
   }
   if (spec->path == AGG_PATH_SORT) {
+    h->last_path = AGG_PATH_SORT;
     // sort path: the control block plus the sort's double buffers fill the budget
     const uint64_t cb = align_up(sizeof(Ctrl), 256);
     if (cudaMalloc(&h->work, cb) != cudaSuccess) {
@@ -402,6 +490,11 @@ agg_status agg_create(size_t budget, const agg_spec* spec, agg_handle** out) {
     agg_destroy(h);
     return st;
   }
+  if (spec->path == AGG_PATH_AUTO) {
+    // the sort path of an AUTO handle works in the same memory, after the control block
+    const uint64_t cb = align_up(sizeof(Ctrl), 256);
+    sort_attach(h->sort, b + cb, L.total - cb);
+  }
   *out = h;
   return AGG_OK;
 }
@@ -419,6 +512,11 @@ agg_status agg_set_tuning(agg_handle* h, const agg_tuning* t) {
                        &ki) != cudaSuccess) {
     cudaGetLastError();
     return AGG_ERR_CUDA;
+  }
+  if (h->stg_mem[0] && e.staging_tier != 0 && (e.staging_tier == 2) != h->stg_host) {
+    // another staging tier: reserved again on the next run
+    cudaDeviceSynchronize();
+    free_staging(h);
   }
   if (ki.blocks > h->ki.blocks && h->stg_mem[0]) {
     // more blocks means more open chunks: re-reserve on the next run
@@ -453,7 +551,9 @@ agg_status agg_run(agg_handle* h, const int64_t* d_keys, const void* d_vals, uin
   const agg_status io = check_device_io(h->spec.ops, h->spec.value_type, d_keys, d_vals, n, out, true);
   if (io != AGG_OK) return io;
 
-  if (h->spec.path == AGG_PATH_SORT) {
+  int path = h->spec.path;
+  if (path == AGG_PATH_AUTO) path = path_costs(&h->spec, h->tune, n, h->budget, h->es, h->slots).choice;
+  if (path == AGG_PATH_SORT) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
       return AGG_ERR_INVALID_ARG;  // the sort path plans on the host between kernels
@@ -462,8 +562,20 @@ agg_status agg_run(agg_handle* h, const int64_t* d_keys, const void* d_vals, uin
                              out, s);
     h->last_stream = s;
     h->ran = true;
+    h->last_path = AGG_PATH_SORT;
+    if (h->spec.path == AGG_PATH_AUTO) h->table_dirty = true;
     return st;
   }
+  if (h->table_dirty) {  // the sort path used the table's memory: clear it first
+    if (hash_init_table(h->ent, h->tags, (uint32_t)h->slots, h->ent_kind, s) != cudaSuccess) {
+      cudaGetLastError();
+      return AGG_ERR_CUDA;
+    }
+    h->launches += 1;
+    h->table_dirty = false;
+    h->dirty_lo = h->slots;
+  }
+  h->last_path = AGG_PATH_HASH;
   return hash_enqueue(h, d_keys, d_vals, n, out, s, false);
 }
 
@@ -526,6 +638,7 @@ agg_status hash_enqueue(agg_handle* h, const int64_t* d_keys, const void* d_vals
   p.cache = h->tune.smem_entries != 1;
   p.dedup = h->tune.warp_dedup == 1 ? 1 : 0;
   p.no_prefetch = host_input ? 1 : 0;
+  p.stg_host = h->stg_host ? 1 : 0;
   hash_fallback_plan(fan, h->tune.max_levels, (uint32_t)h->ki.blocks, h->slots, h->es, p.ns, h->stg_mem[0] != nullptr,
                      &p);
   // the sorted-input path combines block boundaries with atomics on the output
@@ -671,7 +784,9 @@ agg_status agg_get_stats(agg_handle* h, agg_stats* s) {
   s->sorted_input = c.last_sorted;
   s->fallback_records = c.last_fallback_records;
   s->fallback_level = c.last_fallback_level;
-  if (h->spec.path == AGG_PATH_SORT) sort_fill_stats(h->sort, s);
+  s->staging_in_host = h->stg_host ? 1 : 0;
+  s->path = (uint64_t)h->last_path;
+  if (h->last_path == AGG_PATH_SORT) sort_fill_stats(h->sort, s);
   return AGG_OK;
 }
 
@@ -1137,6 +1252,7 @@ struct agg_server {
   RangePool stage;      // their staging areas (outside the budgets, like the paper's disk)
   uint32_t blocks_in_use = 0, big_blocks_in_use = 0;
   uint32_t inject_fail_at = 0;  // test hook: the k-th launch (1-based) fails after its set-up was queued
+  uint32_t sort_epoch = 0;      // look-back epochs of the sort runs (each run's memory is cleared first)
   uint32_t launches = 0;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
@@ -1217,6 +1333,7 @@ struct QueryPlan {
   int in_budget = 0;      // 1 partitioned, 2 single table (ordinary launches, no team), 0 the spilling kernel
   PartPlan pp;
   uint32_t s_fast = 0;
+  bool sort = false;      // the sort path in the query's working memory (one round: no host step)
 };
 
 // Table size, fan-out and staging of a query run by `team` blocks.
@@ -1232,6 +1349,16 @@ QueryPlan plan_query(const agg_server* s, const agg_query& q, uint32_t team) {
   si.expected_groups = q.expected_groups;
   P.fan = plan_fan(&si, s->tune, n, q.budget, s->es);
   P.team = team;
+  if (s->spec.path == AGG_PATH_AUTO &&
+      path_costs(&si, s->tune, n, q.budget, s->es, P.L.slots).choice == AGG_PATH_SORT) {
+    const uint64_t cb = align_up(sizeof(Ctrl), 256);
+    if (n <= sort_rows_for(P.L.total - cb)) {  // one sort round: nothing for the host to plan
+      P.sort = true;
+      P.team = 0;
+      P.may_spill = false;
+      return P;
+    }
+  }
   // every group fits the table at once: the in-budget paths, no staging
   const uint32_t ns = s->tune.smem_entries;
   if (hash_part_plan(n, P.slots, s->es, ns, &P.pp)) {
@@ -1265,6 +1392,27 @@ agg_status server_launch(agg_server* s, ServerQuery& sq, const QueryPlan& P, int
   uint8_t* ent = base + P.L.ent_off;
   const uint64_t n = q.n;
   if (q.ready && cudaStreamWaitEvent(st, static_cast<cudaEvent_t>(q.ready), 0) != cudaSuccess) return AGG_ERR_CUDA;
+  if (P.sort) {  // the sort path, in the query's working memory after its control block
+    if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return AGG_ERR_CUDA;
+    s->launches += 1;
+    if (s->inject_fail_at && s->launches == s->inject_fail_at) return AGG_ERR_CUDA;  // host-injected failure
+    const uint64_t cb = align_up(sizeof(Ctrl), 256);
+    SortState ss{};
+    sort_attach(ss, base + cb, P.L.total - cb);
+    ss.epoch = s->sort_epoch;
+    agg_output o = q.out;
+    o.d_n_groups = nullptr;
+    const agg_status r = sort_run(ss, P.L.total - cb, s->spec, ctrl, q.d_keys, q.d_vals, n, &o, st);
+    s->sort_epoch = ss.epoch;
+    if (r != AGG_OK) return r;
+    if (cudaMemcpyAsync(s->pinned + 2 * slot, &ctrl->status_bits, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(s->pinned + 2 * slot + 1, &ctrl->last_n_groups, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaEventRecord(s->events[slot], st) != cudaSuccess)
+      return AGG_ERR_CUDA;
+    sq.info.team_blocks = 0;
+    sq.info.path = AGG_PATH_SORT;
+    return AGG_OK;
+  }
   // the entries this run uses (and the side slot after them) start empty
   const uint32_t used = P.in_budget == 1 ? P.pp.s_ovf : P.in_budget == 2 ? P.s_fast : (uint32_t)P.slots;
   if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st) != cudaSuccess ||
@@ -1328,6 +1476,7 @@ agg_status server_launch(agg_server* s, ServerQuery& sq, const QueryPlan& P, int
       cudaEventRecord(s->events[slot], st) != cudaSuccess)
     return AGG_ERR_CUDA;
   sq.info.team_blocks = P.team;
+  sq.info.path = AGG_PATH_HASH;
   return AGG_OK;
 }
 
@@ -1345,7 +1494,7 @@ void release_query(agg_server* s, ServerQuery& sq) {
 extern "C" {
 
 agg_status agg_server_create(const agg_spec* spec, size_t pool_bytes, uint32_t max_active, agg_server** out) {
-  if (!out || !valid_spec(spec) || spec->path != AGG_PATH_HASH || max_active == 0 || max_active > 4096 ||
+  if (!out || !valid_spec(spec) || spec->path == AGG_PATH_SORT || max_active == 0 || max_active > 4096 ||
       pool_bytes < AGG_MIN_BUDGET)
     return AGG_ERR_INVALID_ARG;
   *out = nullptr;
@@ -1474,7 +1623,8 @@ agg_status agg_server_progress(agg_server* s, uint32_t* completed) {
     ServerQuery& sq = s->queries[t];
     // A query that fits its table at once runs on the in-budget kernels:
     // ordinary launches that wait on nothing and hold no team.
-    const bool in_budget = plan_query(s, sq.q, 0).in_budget != 0;
+    const QueryPlan P0 = plan_query(s, sq.q, 0);
+    const bool in_budget = P0.in_budget != 0 || P0.sort;
     const uint32_t want = in_budget ? 0u : team_wanted(sq.q.n, all, (uint32_t)s->slot_ticket.size());
     const bool big = want > SMALL_TEAM && s->slot_ticket.size() > 1;
     uint32_t avail = all - s->blocks_in_use;

@@ -130,6 +130,7 @@ struct HashParams {
   uint32_t sorted_probe; // try the sorted-input path first (a sampled order check decides)
   uint32_t max_levels;   // records reaching this level go to the sort fallback
   uint32_t fallback_ok;  // the sort fallback has its shared memory and scratch (else the depth cap is an error)
+  uint32_t stg_host;     // the staging areas are in host memory (reached over the host link)
   uint64_t timeout_ns; // bounded waits give up after this long
 };
 

@@ -1075,6 +1075,7 @@ __device__ __forceinline__ bool staged_record(const HashParams& P, uint32_t src,
 }
 
 __device__ __forceinline__ void prefetch_staged(const HashParams& P, uint32_t src, const Smem& S, uint32_t j) {
+  if (P.stg_host) return;  // staging in host memory: no bulk staging in L2
   prefetch_l2(P.stg[src] + (size_t)S.tl_chunk[j] * CH * REC_BYTES, S.tl_count[j] * (uint32_t)REC_BYTES);
 }
 
@@ -2082,7 +2083,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
       const uint64_t ntiles = c1 - c0;
       if (!grid_barrier(T, C, P.timeout_ns, S)) return false;  // shared-memory rounds before it are complete
       for (uint64_t t = T.bid; t < ntiles; t += T.nb) {
-        if (threadIdx.x == 0 && t + T.nb < ntiles) {  // one tile is one chunk (CH == TILE)
+        if (threadIdx.x == 0 && t + T.nb < ntiles && !P.stg_host) {  // one tile is one chunk (CH == TILE)
           const uint32_t nc = __ldcg(list + c0 + (uint32_t)(t + T.nb));
           prefetch_l2(P.stg[src] + (size_t)nc * CH * REC_BYTES, __ldcg(dcount + nc) * (uint32_t)REC_BYTES);
         }

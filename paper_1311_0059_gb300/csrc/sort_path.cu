@@ -709,6 +709,16 @@ struct Driver {
 
 };
 
+uint64_t rows_fitting(uint64_t avail) {
+  uint64_t lo = 0, hi = MAX_ROUND;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi + 1) / 2;
+    if (work_bytes_for(mid) <= avail) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 uint64_t round_rows_for(size_t budget) {
   // largest round whose working memory fits the budget (minus the control block)
   const uint64_t avail = budget > 65536 ? budget - 65536 : 0;
@@ -723,8 +733,20 @@ uint64_t round_rows_for(size_t budget) {
 
 }  // namespace
 
+uint64_t sort_rows_for(uint64_t work_bytes) { return rows_fitting(work_bytes); }
+
+void sort_attach(SortState& s, void* work, uint64_t work_bytes) {
+  s.work = work;
+  s.work_bytes = work_bytes;
+  s.round_rows = rows_fitting(work_bytes);
+  s.external = true;
+  cudaFuncSetAttribute(reinterpret_cast<const void*>(&onesweep_kernel), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(OnesweepSmem));
+}
+
 agg_status sort_reserve(SortState& s, uint64_t rows, size_t budget, const agg_spec&) {
   // `budget` here is what remains of the handle's budget after its control block
+  if (s.external && s.round_rows < STILE) return AGG_ERR_BUDGET_TOO_SMALL;
   if (!s.work) {
     const uint64_t rr = round_rows_for(budget);
     if (rr < STILE) return AGG_ERR_BUDGET_TOO_SMALL;
@@ -776,6 +798,8 @@ agg_status sort_run(SortState& s, size_t budget, const agg_spec& spec, Ctrl* ctr
   s.last_buckets = s.last_passes = s.last_rounds = s.last_levels = 0;
   d.ok(cudaMemsetAsync(d.w.run_base, 0, 8, stream));
   d.ok(cudaMemsetAsync(d.w.err, 0, 8, stream));
+  if (s.external)  // memory another path used: no stale look-back word may match an epoch
+    d.ok(cudaMemsetAsync(d.w.status, 0, ((s.round_rows + STILE - 1) / STILE + 1) * 256 * 8, stream));
   const long long* keys = reinterpret_cast<const long long*>(d_keys);
   if (n > 0) {
     if (n <= s.round_rows) {
@@ -793,7 +817,7 @@ agg_status sort_run(SortState& s, size_t budget, const agg_spec& spec, Ctrl* ctr
 
 void sort_free(SortState& s) {
   if (s.mem) cudaFree(s.mem);
-  if (s.work) cudaFree(s.work);
+  if (s.work && !s.external) cudaFree(s.work);
   const uint64_t l = s.launches, e = s.epoch;
   s = SortState{};
   s.launches = l;

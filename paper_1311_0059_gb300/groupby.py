@@ -207,9 +207,9 @@ class Server:
     their declared budgets and run concurrently (agg_server_*)."""
 
     def __init__(self, pool_bytes: int, max_active: int = 64, ops: int = ALL_OPS, value_type: int = AGG_I64,
-                 seed: int = 0):
+                 seed: int = 0, path: int = AGG_PATH_HASH):
         self.lib = _abi.load()
-        self.spec = make_spec(ops, value_type, AGG_PATH_HASH, 0, seed)
+        self.spec = make_spec(ops, value_type, path, 0, seed)
         self.ops = ops
         h = ctypes.c_void_p()
         check(self.lib.agg_server_create(ctypes.byref(self.spec), pool_bytes, max_active, ctypes.byref(h)),

@@ -117,5 +117,30 @@ def test_depth_cap_knob_is_checked_on_the_host(lib):
     for bad in (12, 100):
         with pytest.raises(_abi.AggError):
             gb.plan(64 << 20, 10, spec, _abi.agg_tuning(max_levels=bad))
+    for tier in (0, 1, 2):
+        gb.plan(64 << 20, 10, spec, _abi.agg_tuning(staging_tier=tier))
     with pytest.raises(_abi.AggError):
-        gb.plan(64 << 20, 10, spec, _abi.agg_tuning(reserved=1))
+        gb.plan(64 << 20, 10, spec, _abi.agg_tuning(staging_tier=3))
+
+
+def test_cost_model_chooses_between_the_paths(lib):
+    # AGG_PATH_AUTO: the model in bytes (input, the Pre-Partitioning spill
+    # R(1 - K/G) written and read, the level-1 sort when groups exceed 0.8 of
+    # the rows, the result) against the sort path's passes, over each path's
+    # measured bandwidth.  Nearly unique keys that spill pick the sort path; low
+    # cardinality, small inputs and an unknown G pick the hash path.
+    from paper_1311_0059_gb300 import groupby as gb, _abi
+    auto = lambda g: gb.make_spec(ops=15, value_type=_abi.AGG_I64, path=_abi.AGG_PATH_AUTO, expected_groups=g)
+    p = gb.plan(128 << 20, 3_000_000, auto(3_000_000))
+    assert p["chosen_path"] == _abi.AGG_PATH_SORT and p["sort_seconds"] < p["hash_seconds"]
+    assert p["hash_bytes"] > 16 * 3_000_000 + 2 * 16 * 1_900_000          # input and the spill both ways
+    p = gb.plan(128 << 20, 3_000_000, auto(300_000))
+    assert p["chosen_path"] == _abi.AGG_PATH_HASH and p["hash_seconds"] < p["sort_seconds"]
+    assert gb.plan(128 << 20, 3_000_000, auto(0))["chosen_path"] == _abi.AGG_PATH_HASH   # G unknown
+    assert gb.plan(128 << 20, 50_000, auto(50_000))["chosen_path"] == _abi.AGG_PATH_HASH  # fits the table
+    assert gb.plan(256 << 20, 200_000_000, auto(49_000_000))["chosen_path"] == _abi.AGG_PATH_HASH
+    assert gb.plan(256 << 20, 50_000_000, auto(50_000_000))["chosen_path"] == _abi.AGG_PATH_SORT
+    # the fixed paths report themselves
+    assert gb.plan(128 << 20, 3_000_000, gb.make_spec(path=_abi.AGG_PATH_HASH, expected_groups=3_000_000)
+                   )["chosen_path"] == _abi.AGG_PATH_HASH
+    assert gb.plan(128 << 20, 100, gb.make_spec(path=_abi.AGG_PATH_SORT))["chosen_path"] == _abi.AGG_PATH_SORT
