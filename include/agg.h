@@ -355,13 +355,18 @@ agg_status agg_server_submit(agg_server* s, const agg_query* q, uint64_t* ticket
  * declared budget fits the free pool, its staging (if it may spill) fits the
  * staging pool, and enough thread blocks are free: the teams of running queries
  * never add up to more blocks than the GPU holds at once, so their cooperative
- * grids never wait on one another.  A query wants about one block per 64k rows
- * (a power of two, 8 to the whole GPU) and gets fewer when fewer are free (at
- * least 8, or all it wants if less).  Queries wanting more than 32 blocks share
- * all but a quarter of the blocks, which stays free for the small ones; such a
- * query waiting for blocks does not hold back the smaller queries behind it,
- * while one waiting for memory holds back every later query.  Non-blocking.
- * *completed (may be NULL) receives the number of queries finished now. */
+ * grids never wait on one another.  A query whose groups all fit its table at
+ * once (n at most half its slots) runs on the in-budget kernels, ordinary
+ * launches that hold no team; so does a query an AGG_PATH_AUTO server sends to
+ * the sort path (only when one sort round holds it).  Any other query wants
+ * about one block per 8k rows (a power of two, 8 to the whole GPU) and gets
+ * fewer when fewer are free (at least 8, or all it wants if less), or when its
+ * staging (one open chunk per block and partition) would not fit the staging
+ * pool.  Queries wanting more than 32 blocks share all but a quarter of the
+ * blocks, which stays free for the small ones; such a query waiting for blocks
+ * does not hold back the smaller queries behind it, while one waiting for
+ * memory holds back every later query.  Non-blocking.  *completed (may be NULL)
+ * receives the number of queries finished now. */
 agg_status agg_server_progress(agg_server* s, uint32_t* completed);
 
 /* State, result size and timestamps of a query. */

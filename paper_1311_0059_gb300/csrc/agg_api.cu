@@ -1635,7 +1635,13 @@ agg_status agg_server_progress(agg_server* s, uint32_t* completed) {
       ++it;
       continue;
     }
-    const QueryPlan P = plan_query(s, sq.q, team);
+    QueryPlan P = plan_query(s, sq.q, team);
+    // a spilling query reserves one open staging chunk per block and partition:
+    // a smaller team when that would not fit the staging pool at all
+    for (uint32_t tm = team; P.stg_len > s->stage.bytes && tm > 8;) {
+      tm /= 2;
+      P = plan_query(s, sq.q, tm);
+    }
     uint64_t off = 0, soff = 0;
     if (!pool_alloc(s->pool, P.L.total, &off)) break;
     if (!pool_alloc(s->stage, P.stg_len, &soff)) {
