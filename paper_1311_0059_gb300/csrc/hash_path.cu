@@ -963,6 +963,42 @@ __device__ __forceinline__ bool sub_upsert(const Cache& cc, long long key, uint6
   return false;
 }
 
+// As sub_upsert, for a partial state of c rows (sum s, extremes mn and mx).
+template <int ENT>
+__device__ __forceinline__ bool sub_upsert_part(const Cache& cc, long long key, uint64_t h, uint32_t c,
+                                                unsigned long long s, long long mn, long long mx) {
+  if (key == SKEY_EMPTY) return false;
+  uint32_t g = ((uint32_t)(h >> 32) & (cc.n / 4 - 1)) * 4;
+#pragma unroll 1
+  for (int step = 0; step < 4; ++step) {
+    long long kk[4];
+    sh_ld_volatile_s64x2(cc.key + g, kk[0], kk[1]);
+    sh_ld_volatile_s64x2(cc.key + g + 2, kk[2], kk[3]);
+    int idx = -1;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      if (idx >= 0) continue;
+      long long x = kk[w];
+      if (x == SKEY_EMPTY) {
+        x = sh_cas_s64(cc.key + g + w, SKEY_EMPTY, key);
+        if (x == SKEY_EMPTY) x = key;
+      }
+      if (x == key) idx = (int)(g + w);
+    }
+    if (idx >= 0) {
+      sh_red_add_u32(cc.cnt + idx, c);
+      smem_add_u64(cc.sum + idx, s);
+      if (Ent<ENT>::MM) {
+        sh_red_min_s64(cc.mn + idx, mn);
+        sh_red_max_s64(cc.mx + idx, mx);
+      }
+      return true;
+    }
+    g = (g + 4) & (cc.n - 1);
+  }
+  return false;
+}
+
 // Writes the groups of the shared-memory table to the output and clears it.
 // Each warp takes a contiguous slice of the slots and reserves its output rows
 // with one atomic of its own, so that no block-wide scan is needed; one block
@@ -2179,7 +2215,16 @@ __global__ void __launch_bounds__(THREADS, 2)
 // and the emit as a second ordinary launch behind it in the stream.  Hot keys
 // are absorbed by the per-block shared-memory cache as at level 0.
 
-constexpr int FAST_RPT = 8;                              // rows per thread of the aggregation pass
+#ifndef AGG_FAST_RPT
+#define AGG_FAST_RPT 8
+#endif
+#ifndef AGG_PART_ROWS_X
+#define AGG_PART_ROWS_X 1
+#endif
+#ifndef AGG_PART_DEDUP
+#define AGG_PART_DEDUP 0
+#endif
+constexpr int FAST_RPT = AGG_FAST_RPT;                     // rows per thread of the aggregation pass
 constexpr uint32_t FAST_ROWS = (uint32_t)THREADS * FAST_RPT;  // rows per block
 constexpr int EMIT_THREADS = 256;
 constexpr uint32_t EMIT_SLOTS = (uint32_t)EMIT_THREADS * 16;  // slots per emit block (16 tag bytes a thread)
@@ -2622,6 +2667,43 @@ __global__ void __launch_bounds__(THREADS, 2)
         v[j] = x.y;
       }
     }
+#if AGG_PART_DEDUP
+    // rows of equal keys in a warp are combined first: the lowest lane of each
+    // key carries their partial state into the tables
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const uint32_t vm = __ballot_sync(FULL_MASK, in[j]);
+      uint32_t peers = 0;
+      if (in[j]) peers = __match_any_sync(vm, k[j]);
+      const uint32_t leader = in[j] ? (uint32_t)__ffs(peers) - 1 : lane;
+      const uint32_t gsize = __popc(peers);
+      const uint32_t maxg = __reduce_max_sync(FULL_MASK, gsize);
+      unsigned long long gs = (unsigned long long)v[j];
+      long long gmn = v[j], gmx = v[j];
+      uint32_t rem = (in[j] && lane == leader) ? (peers & ~(1u << lane)) : 0u;
+      for (uint32_t it = 1; it < maxg; ++it) {
+        const int src = rem ? __ffs(rem) - 1 : (int)lane;
+        rem &= rem - 1;
+        const long long ov = __shfl_sync(FULL_MASK, v[j], src);
+        if (src != (int)lane) {
+          gs += (unsigned long long)ov;
+          gmn = ov < gmn ? ov : gmn;
+          gmx = ov > gmx ? ov : gmx;
+        }
+      }
+      if (!in[j] || lane != leader) continue;
+      const uint64_t h = fmix64((uint64_t)k[j] ^ seed0);
+      if (sub_upsert_part<ENT>(cc, k[j], h, gsize, gs, gmn, gmx)) continue;
+      uint32_t sl = fast_home(h, s_ovf);
+      const long long k2 =
+          k[j] == EMPTY_KEY ? EMPTY_KEY : __ldcg(reinterpret_cast<const long long*>(Ent<ENT>::at(P.ent, sl)));
+      sl = fast_probe<ENT>(P, s_ovf, k[j], h, sl, k2);
+      Ent<ENT>::add(Ent<ENT>::at(P.ent, sl), P.ops, gsize, gs, gmn, gmx);
+      if (k[j] == EMPTY_KEY) side = true;
+      else ovf = true;
+    }
+#else
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       if (!in[j]) continue;
@@ -2635,6 +2717,7 @@ __global__ void __launch_bounds__(THREADS, 2)
       if (k[j] == EMPTY_KEY) side = true;
       else ovf = true;
     }
+#endif
   }
   if (ovf) atomicOr(&C->overflow_used[0], 1u);
   if (side) atomicOr(&C->overflow_used[1], 1u);
@@ -2855,7 +2938,7 @@ bool hash_part_plan(uint64_t n, uint64_t slots, uint32_t es, uint32_t ns, PartPl
   PartPlan pp;
   pp.nblk = (uint32_t)((n + FAST_ROWS - 1) / FAST_ROWS);
   uint32_t plog = 0;
-  while ((1ull << plog) * ns < n && (1u << plog) < PART_MAX) ++plog;  // about ns rows per partition
+  while ((1ull << plog) * ns * AGG_PART_ROWS_X < n && (1u << plog) < PART_MAX) ++plog;  // about ns rows each
   pp.plog = plog;
   uint64_t ovf = n + n / 4 > MIN_SLOTS ? n + n / 4 : MIN_SLOTS;  // at most n keys overflow: always room
   ovf = (ovf + BUCKET - 1) / BUCKET * BUCKET;
