@@ -53,7 +53,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="spill", choices=sorted(WORKLOADS) + ["batched", "served"])
+    ap.add_argument("--workload", default="spill", choices=sorted(WORKLOADS) + ["sorted", "batched", "served"])
     ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of Poisson arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="served: queries per second")
     ap.add_argument("--max-active", type=int, default=64, help="served: queries running at once")
@@ -71,10 +71,12 @@ def parse_args(argv=None):
 
 
 def workload(args, rank=0) -> dg.Workload:
-    base = WORKLOADS[args.workload]
+    base = WORKLOADS["spill" if args.workload == "sorted" else args.workload]
     w = dg.Workload(base.name, n=args.rows or base.n, domain=args.domain or base.domain, dist=base.dist,
                     zipf_s=base.zipf_s, vtype=base.vtype, seed=base.seed + rank, budget=args.budget or base.budget,
                     ops=base.ops)
+    if args.workload == "sorted":
+        w.name = "sorted input: " + base.name + " (rows reordered by key before timing)"
     if args.rows or args.domain or args.budget:
         w.name = f"{w.dist} {w.n} rows over {w.domain} keys, budget {w.budget >> 20} MiB"
     return w
@@ -285,9 +287,10 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ our arm
 
-def make_inputs(w: dg.Workload, vt: int, dev, stream):
+def make_inputs(w: dg.Workload, vt: int, dev, stream, sort_keys: bool = False):
     """Device inputs of w; a small input is copied enough times that rotating
-    through the copies streams more than twice the L2 per pass."""
+    through the copies streams more than twice the L2 per pass.  sort_keys
+    reorders the rows by key (input preparation, before any timing)."""
     import torch
     from paper_1311_0059_gb300 import AGG_I32
     copies = 1 if w.n * 16 > 2 * L2_BYTES else max(2, (4 * L2_BYTES) // max(w.n * 12, 1) + 1)
@@ -299,6 +302,10 @@ def make_inputs(w: dg.Workload, vt: int, dev, stream):
             cdf = torch.from_numpy(w.cdf()).to(dev)
         w.device(k.data_ptr(), v.data_ptr(), cdf_ptr=cdf.data_ptr() if cdf is not None else 0,
                  stream_handle=stream.cuda_stream)
+        if sort_keys:
+            k, order = torch.sort(k)
+            v = v[order]
+            del order
         keys.append(k)
         vals.append(v)
     torch.cuda.synchronize()
@@ -309,7 +316,8 @@ PATH_KERNELS = {0: "hash_groupby_kernel", 1: "part_scatter_kernel + part_agg_ker
                 2: "fast_agg_kernel + fast_emit_kernel"}
 
 
-def measure_hash(w: dg.Workload, steps: int, warmup: int, world: int, local: int, dev, stream) -> dict:
+def measure_hash(w: dg.Workload, steps: int, warmup: int, world: int, local: int, dev, stream,
+                 sort_keys: bool = False) -> dict:
     """One agg_run per step over w's rows, resident in HBM, timed with CUDA
     events on the launching stream; the roofline counts input, spill written,
     spill read and result bytes.  Returns the record and the live objects."""
@@ -319,7 +327,7 @@ def measure_hash(w: dg.Workload, steps: int, warmup: int, world: int, local: int
     from paper_1311_0059_gb300.groupby import GroupBy, make_spec, plan
 
     vt = AGG_I32 if w.vtype == "i32_1000" else AGG_I64
-    keys, vals = make_inputs(w, vt, dev, stream)
+    keys, vals = make_inputs(w, vt, dev, stream, sort_keys)
     copies = len(keys)
     g = GroupBy(w.budget, ops=w.ops, value_type=vt, path=AGG_PATH_HASH)
     g.reserve(w.n)
@@ -368,7 +376,8 @@ def measure_hash(w: dg.Workload, steps: int, warmup: int, world: int, local: int
                                 "spill_read": stats["spill_bytes_read"], "result": out_b}}
     rec = {"workload": w.name, "rows_per_s": rows_total / (ms_max / 1e3), "ms_per_run": ms_max / steps,
            "steps": steps, "roofline": roof, "gpu_launches": gpu_launches, "n_groups": n_groups,
-           "in_budget_path": path, "levels": stats["levels"], "clocks": clocks.summary(),
+           "in_budget_path": path, "levels": stats["levels"], "sorted_input_path": stats["sorted_input"],
+           "fallback_records": stats["fallback_records"], "clocks": clocks.summary(),
            "l2": "inputs larger than L2, no flush" if copies == 1 else f"{copies} input copies rotated to defeat L2"}
     if spill_b:
         k_cap = stats["table_capacity"]
@@ -463,7 +472,8 @@ def run_ours(args):
     w = workload(args, rank)
     stream = torch.cuda.current_stream()
 
-    rec, live = measure_hash(w, args.steps, args.warmup, world, local, dev, stream)
+    rec, live = measure_hash(w, args.steps, args.warmup, world, local, dev, stream,
+                             sort_keys=args.workload == "sorted")
     line = {"metric": METRIC, "value": rec["rows_per_s"], "unit": "rows/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": rec["ms_per_run"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64",
@@ -499,12 +509,15 @@ def run_ours(args):
     # one record per other workload, in the same line
     if not args.no_sub and args.workload == "spill" and not (args.rows or args.domain or args.budget):
         configs = {}
-        for name, wl, steps in (("plain", dg.PLAIN_1M_10K, max(args.steps, 200)),
-                                ("skewed", dg.ZIPF_500M_10M, args.steps)):
+        for name, wl, steps, srt in (("plain", dg.PLAIN_1M_10K, max(args.steps, 200), False),
+                                     ("skewed", dg.ZIPF_500M_10M, args.steps, False),
+                                     ("sorted", dg.SPILL_200M_50M, args.steps, True)):
             wr = dg.Workload(wl.name, n=wl.n, domain=wl.domain, dist=wl.dist, zipf_s=wl.zipf_s, vtype=wl.vtype,
                              seed=wl.seed + rank, budget=wl.budget, ops=wl.ops)
+            if srt:
+                wr.name = "sorted input: " + wl.name + " (rows reordered by key before timing)"
             try:
-                r, lv = measure_hash(wr, steps, args.warmup, world, local, dev, stream)
+                r, lv = measure_hash(wr, steps, args.warmup, world, local, dev, stream, sort_keys=srt)
                 release(lv)
                 configs[name] = r
             except Exception as e:

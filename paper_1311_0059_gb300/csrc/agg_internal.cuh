@@ -78,7 +78,7 @@ struct alignas(128) Ctrl {
   unsigned int sorted_used;               // sorted-input path: this run completed on it
   unsigned long long sorted_heads[MAX_GRID];  // sorted-input path: segment heads in each block's rows
   unsigned int fallback_now;              // this level's records go to the sort fallback
-  unsigned int pad_fb;
+  unsigned int ovf_listed;                // in-budget partitions: overflow-table slots claimed (listed)
   unsigned long long fallback_records;    // records aggregated by the sort fallback
   unsigned long long fallback_level;      // level at which it ran (0 = none)
   // ---- snapshot of the last completed run

@@ -2218,8 +2218,11 @@ __global__ void __launch_bounds__(THREADS, 2)
 #ifndef AGG_FAST_RPT
 #define AGG_FAST_RPT 8
 #endif
-#ifndef AGG_PART_ROWS_X
-#define AGG_PART_ROWS_X 1
+#ifndef AGG_PART_ROWS_NUM
+#define AGG_PART_ROWS_NUM 1
+#endif
+#ifndef AGG_PART_ROWS_DEN
+#define AGG_PART_ROWS_DEN 1
 #endif
 #ifndef AGG_PART_DEDUP
 #define AGG_PART_DEDUP 0
@@ -2240,7 +2243,7 @@ __device__ __forceinline__ uint32_t fast_home(uint64_t h, uint32_t s_act) {
 // tag byte, which marks it for the emit.
 template <int ENT>
 __device__ __forceinline__ uint32_t fast_probe(const HashParams& P, uint32_t s_act, long long key, uint64_t h,
-                                               uint32_t slot, long long k2) {
+                                               uint32_t slot, long long k2, bool* claimed = nullptr) {
   if (key == EMPTY_KEY) {  // the empty marker value itself: side slot
     uint8_t* tb = reinterpret_cast<uint8_t*>(P.tags) + P.slots;
     if (__ldcg(tb) == 0) __stcg(tb, (uint8_t)0x80);
@@ -2254,6 +2257,7 @@ __device__ __forceinline__ uint32_t fast_probe(const HashParams& P, uint32_t s_a
                                                  (unsigned long long)EMPTY_KEY, (unsigned long long)key);
       if (old == EMPTY_KEY) {
         __stcg(reinterpret_cast<uint8_t*>(P.tags) + slot, (uint8_t)key_tag(h));
+        if (claimed) *claimed = true;
         return slot;
       }
       if (old == key) return slot;
@@ -2449,6 +2453,7 @@ __global__ void __launch_bounds__(EMIT_THREADS) fast_emit_kernel(const HashParam
 // block to finish emits that table when it was used, then publishes the count.
 
 constexpr uint32_t PART_MAX = 2048;      // most partitions
+constexpr uint32_t OVF_LIST = 65536;     // overflow-table slots listed for the emit (a scan past that)
 constexpr uint32_t PART_MAX_BLK = 512;   // most first-launch blocks (2M rows)
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -2615,7 +2620,8 @@ __device__ void block_emit_table(const HashParams& P, uint32_t s_act) {
 template <int ENT>
 __global__ void __launch_bounds__(THREADS, 2)
     part_agg_kernel(const HashParams P, uint32_t plog, uint32_t nblk, const longlong2* __restrict__ rec,
-                    const uint32_t* __restrict__ gcnt, const uint32_t* __restrict__ gstart, uint32_t s_ovf) {
+                    const uint32_t* __restrict__ gcnt, const uint32_t* __restrict__ gstart, uint32_t s_ovf,
+                    uint32_t* __restrict__ ovf_list) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t pre[PART_MAX_BLK + 1];
   __shared__ uint32_t sst[PART_MAX_BLK];
@@ -2698,8 +2704,13 @@ __global__ void __launch_bounds__(THREADS, 2)
       uint32_t sl = fast_home(h, s_ovf);
       const long long k2 =
           k[j] == EMPTY_KEY ? EMPTY_KEY : __ldcg(reinterpret_cast<const long long*>(Ent<ENT>::at(P.ent, sl)));
-      sl = fast_probe<ENT>(P, s_ovf, k[j], h, sl, k2);
+      bool claimed = false;
+      sl = fast_probe<ENT>(P, s_ovf, k[j], h, sl, k2, &claimed);
       Ent<ENT>::add(Ent<ENT>::at(P.ent, sl), P.ops, gsize, gs, gmn, gmx);
+      if (claimed) {
+        const uint32_t at = atomicAdd(&C->ovf_listed, 1u);
+        if (at < OVF_LIST) ovf_list[at] = sl;
+      }
       if (k[j] == EMPTY_KEY) side = true;
       else ovf = true;
     }
@@ -2712,8 +2723,13 @@ __global__ void __launch_bounds__(THREADS, 2)
       uint32_t sl = fast_home(h, s_ovf);
       const long long k2 =
           k[j] == EMPTY_KEY ? EMPTY_KEY : __ldcg(reinterpret_cast<const long long*>(Ent<ENT>::at(P.ent, sl)));
-      sl = fast_probe<ENT>(P, s_ovf, k[j], h, sl, k2);
+      bool claimed = false;
+      sl = fast_probe<ENT>(P, s_ovf, k[j], h, sl, k2, &claimed);
       Ent<ENT>::add(Ent<ENT>::at(P.ent, sl), P.ops, 1ull, (unsigned long long)v[j], v[j], v[j]);
+      if (claimed) {
+        const uint32_t at = atomicAdd(&C->ovf_listed, 1u);
+        if (at < OVF_LIST) ovf_list[at] = sl;
+      }
       if (k[j] == EMPTY_KEY) side = true;
       else ovf = true;
     }
@@ -2730,7 +2746,21 @@ __global__ void __launch_bounds__(THREADS, 2)
   __syncthreads();
   if (!last) return;
   __threadfence();
-  if (ld_acquire_u32(&C->overflow_used[0])) block_emit_table<ENT>(P, s_ovf);
+  if (ld_acquire_u32(&C->overflow_used[0])) {
+    const uint32_t listed = ld_acquire_u32(&C->ovf_listed);
+    if (listed <= OVF_LIST) {  // the claimed slots are listed: emit just those
+      __shared__ unsigned long long list_base;
+      if (threadIdx.x == 0) list_base = atomicAdd(&C->out_count, (unsigned long long)listed);
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < listed; i += THREADS) {
+        const uint32_t sl = __ldcg(ovf_list + i);
+        emit_one<ENT>(P, Ent<ENT>::at(P.ent, sl), list_base + i);
+        __stcg(reinterpret_cast<uint8_t*>(P.tags) + sl, (uint8_t)0);
+      }
+    } else {
+      block_emit_table<ENT>(P, s_ovf);
+    }
+  }
   if (threadIdx.x == 0 && ld_acquire_u32(&C->overflow_used[1])) {
     uint8_t* tb = reinterpret_cast<uint8_t*>(P.tags) + P.slots;
     if (__ldcg(tb)) {
@@ -2762,6 +2792,7 @@ __global__ void __launch_bounds__(THREADS, 2)
   C->last_fallback_level = 0;
   C->overflow_used[0] = 0;
   C->overflow_used[1] = 0;
+  C->ovf_listed = 0;
   C->out_count = 0;
   __threadfence();
   C->done_count = 0;
@@ -2938,13 +2969,14 @@ bool hash_part_plan(uint64_t n, uint64_t slots, uint32_t es, uint32_t ns, PartPl
   PartPlan pp;
   pp.nblk = (uint32_t)((n + FAST_ROWS - 1) / FAST_ROWS);
   uint32_t plog = 0;
-  while ((1ull << plog) * ns * AGG_PART_ROWS_X < n && (1u << plog) < PART_MAX) ++plog;  // about ns rows each
+  // rows per partition: about ns * AGG_PART_ROWS_NUM / AGG_PART_ROWS_DEN
+  while ((1ull << plog) * ns * AGG_PART_ROWS_NUM < n * AGG_PART_ROWS_DEN && (1u << plog) < PART_MAX) ++plog;
   pp.plog = plog;
   uint64_t ovf = n + n / 4 > MIN_SLOTS ? n + n / 4 : MIN_SLOTS;  // at most n keys overflow: always room
   ovf = (ovf + BUCKET - 1) / BUCKET * BUCKET;
   pp.s_ovf = (uint32_t)ovf;
   const uint64_t rec_bytes = (uint64_t)pp.nblk * FAST_ROWS * 16;
-  const uint64_t idx_bytes = 2ull * ((uint64_t)pp.nblk << plog) * 4;
+  const uint64_t idx_bytes = 2ull * ((uint64_t)pp.nblk << plog) * 4 + (uint64_t)OVF_LIST * 4;
   const uint64_t scratch_slots = (rec_bytes + idx_bytes + 256 + es - 1) / es + 8;
   if (ovf + 1 + scratch_slots > slots) return false;  // the overflow table, then its side slot, stay clear
   pp.scratch_slot = (uint32_t)(slots - scratch_slots);  // scratch at the top of the entry memory
@@ -2977,7 +3009,8 @@ cudaError_t hash_part_launch(int ent_kind, int vt, const HashParams& p, const Pa
   const longlong2* crec = rec;
   const uint32_t* ccnt = gcnt;
   const uint32_t* cstart = gstart;
-  void* args[] = {const_cast<HashParams*>(&p), &plog, &nblk, &crec, &ccnt, &cstart, &s_ovf};
+  uint32_t* olist = gstart + ((size_t)pp.nblk << pp.plog);
+  void* args[] = {const_cast<HashParams*>(&p), &plog, &nblk, &crec, &ccnt, &cstart, &s_ovf, &olist};
   return cudaLaunchKernelExC(&cfg, pick_part_agg(ent_kind), args);
 }
 
