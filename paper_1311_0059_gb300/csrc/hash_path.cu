@@ -122,6 +122,24 @@ __device__ __forceinline__ void sh_red_max_s64(long long* p, long long v) {
   asm volatile("red.shared.max.s64 [%0], %1;" ::"r"(sh_addr(p)), "l"(v) : "memory");
 }
 
+// MIN and MAX in shared memory only ever move one way, so an update that does
+// not improve the value read first is a no-op and is skipped: a value at or
+// above the minimum seen now is at or above the final minimum.  Most rows of a
+// hot key then touch the word with a plain load instead of an atomic.
+__device__ __forceinline__ long long sh_ld_volatile_s64(const long long* p) {
+  long long v;
+  asm volatile("ld.volatile.shared.s64 %0, [%1];" : "=l"(v) : "r"((uint32_t)__cvta_generic_to_shared(p)) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void sh_min_s64(long long* p, long long v) {
+  if (v < sh_ld_volatile_s64(p)) sh_red_min_s64(p, v);
+}
+
+__device__ __forceinline__ void sh_max_s64(long long* p, long long v) {
+  if (v > sh_ld_volatile_s64(p)) sh_red_max_s64(p, v);
+}
+
 __device__ __forceinline__ void smem_add_u64(unsigned long long* p, unsigned long long v) {
   uint32_t* w = reinterpret_cast<uint32_t*>(p);
   const uint32_t lo = (uint32_t)v;
@@ -454,8 +472,8 @@ __device__ __forceinline__ bool cache_hit(const Cache& cc, long long key, uint64
   sh_red_add_u32(cc.cnt + idx, (uint32_t)c);
   smem_add_u64(cc.sum + idx, s);
   if (Ent<ENT>::MM) {
-    sh_red_min_s64(cc.mn + idx, mn);
-    sh_red_max_s64(cc.mx + idx, mx);
+    sh_min_s64(cc.mn + idx, mn);
+    sh_max_s64(cc.mx + idx, mx);
   }
   return true;
 }
@@ -953,8 +971,8 @@ __device__ __forceinline__ bool sub_upsert(const Cache& cc, long long key, uint6
       sh_red_add_u32(cc.cnt + idx, 1u);
       smem_add_u64(cc.sum + idx, (unsigned long long)v);
       if (Ent<ENT>::MM) {
-        sh_red_min_s64(cc.mn + idx, v);
-        sh_red_max_s64(cc.mx + idx, v);
+        sh_min_s64(cc.mn + idx, v);
+        sh_max_s64(cc.mx + idx, v);
       }
       return true;
     }
@@ -989,8 +1007,8 @@ __device__ __forceinline__ bool sub_upsert_part(const Cache& cc, long long key, 
       sh_red_add_u32(cc.cnt + idx, c);
       smem_add_u64(cc.sum + idx, s);
       if (Ent<ENT>::MM) {
-        sh_red_min_s64(cc.mn + idx, mn);
-        sh_red_max_s64(cc.mx + idx, mx);
+        sh_min_s64(cc.mn + idx, mn);
+        sh_max_s64(cc.mx + idx, mx);
       }
       return true;
     }
@@ -2964,8 +2982,11 @@ cudaError_t hash_fast_launch(int ent_kind, int vt, const HashParams& p, uint32_t
   return cudaGetLastError();
 }
 
+#ifndef AGG_PART_OFF
+#define AGG_PART_OFF 0
+#endif
 bool hash_part_plan(uint64_t n, uint64_t slots, uint32_t es, uint32_t ns, PartPlan* out) {
-  if (n == 0 || n > (uint64_t)PART_MAX_BLK * FAST_ROWS || ns < 256) return false;
+  if (AGG_PART_OFF || n == 0 || n > (uint64_t)PART_MAX_BLK * FAST_ROWS || ns < 256) return false;
   PartPlan pp;
   pp.nblk = (uint32_t)((n + FAST_ROWS - 1) / FAST_ROWS);
   uint32_t plog = 0;
