@@ -1288,7 +1288,18 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
   for (uint32_t it = 0;; ++it) {
     const uint32_t sbi = S.sub_q[it & 1];
     if (sbi >= nsub) break;
-    if (threadIdx.x == 0) S.sub_q[(it + 1) & 1] = atomicAdd(&C->sub_next[par], 1u);
+    if (threadIdx.x == 0) {
+      // claim the next sub-partition and stage its records in L2 while this one runs
+      const uint32_t nx = atomicAdd(&C->sub_next[par], 1u);
+      S.sub_q[(it + 1) & 1] = nx;
+      if (nx < nsub) {
+        const uint32_t a = __ldcg(&C->sub_base[par][nx]), b = __ldcg(&C->sub_base[par][nx + 1]);
+        if (a < b && b <= tot) {
+          for (uint32_t o = a; o < b; o += 4096)  // bulk prefetches of at most 64 KiB
+            prefetch_l2(scratch + o, (b - o < 4096u ? b - o : 4096u) * (uint32_t)REC_BYTES);
+        }
+      }
+    }
     uint32_t lo = __ldcg(&C->sub_base[par][sbi]), hi = __ldcg(&C->sub_base[par][sbi + 1]);
     if (hi > tot || lo > hi) {  // inconsistent offsets: report, never read past the scratch
       if (threadIdx.x == 0) set_status(C, AGG_ERR_INTERNAL);
@@ -2471,7 +2482,8 @@ __global__ void __launch_bounds__(EMIT_THREADS) fast_emit_kernel(const HashParam
 // block to finish emits that table when it was used, then publishes the count.
 
 constexpr uint32_t PART_MAX = 2048;      // most partitions
-constexpr uint32_t OVF_LIST = 65536;     // overflow-table slots listed for the emit (a scan past that)
+constexpr uint32_t OVF_LIST = 65536;     // overflow-table slots listed for the last block (a scan past that)
+constexpr uint32_t OVF_BLOCK = 2048;     // overflow-table slots a block lists and emits itself
 constexpr uint32_t PART_MAX_BLK = 512;   // most first-launch blocks (2M rows)
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -2645,9 +2657,15 @@ __global__ void __launch_bounds__(THREADS, 2)
   __shared__ uint32_t sst[PART_MAX_BLK];
   __shared__ uint32_t wsum[WARPS + 1];
   __shared__ uint32_t last;
+  // overflow-table slots this block claimed: every row of a key lies in one
+  // partition, so only this block updates them and it emits them itself
+  __shared__ uint32_t my_ovf[OVF_BLOCK];
+  __shared__ uint32_t my_ovf_n;
+  __shared__ unsigned long long my_ovf_base;
   Ctrl* C = P.ctrl;
   const Cache cc = carve_cache(smem_raw + ((sizeof(Smem) + 15) & ~size_t(15)), P.ns, Ent<ENT>::MM);
   const uint32_t q = blockIdx.x;
+  if (threadIdx.x == 0) my_ovf_n = 0;
   const uint64_t seed0 = level_seed(P.seed, 0);
   for (uint32_t i = threadIdx.x; i < cc.n; i += THREADS) {
     cc.key[i] = SKEY_EMPTY;
@@ -2726,11 +2744,16 @@ __global__ void __launch_bounds__(THREADS, 2)
       sl = fast_probe<ENT>(P, s_ovf, k[j], h, sl, k2, &claimed);
       Ent<ENT>::add(Ent<ENT>::at(P.ent, sl), P.ops, gsize, gs, gmn, gmx);
       if (claimed) {
-        const uint32_t at = atomicAdd(&C->ovf_listed, 1u);
-        if (at < OVF_LIST) ovf_list[at] = sl;
+        const uint32_t mine = atomicAdd(&my_ovf_n, 1u);
+        if (mine < OVF_BLOCK) {
+          my_ovf[mine] = sl;
+        } else {  // more than the block's list: the last block emits these
+          const uint32_t at = atomicAdd(&C->ovf_listed, 1u);
+          if (at < OVF_LIST) ovf_list[at] = sl;
+          ovf = true;
+        }
       }
       if (k[j] == EMPTY_KEY) side = true;
-      else ovf = true;
     }
 #else
 #pragma unroll
@@ -2745,11 +2768,16 @@ __global__ void __launch_bounds__(THREADS, 2)
       sl = fast_probe<ENT>(P, s_ovf, k[j], h, sl, k2, &claimed);
       Ent<ENT>::add(Ent<ENT>::at(P.ent, sl), P.ops, 1ull, (unsigned long long)v[j], v[j], v[j]);
       if (claimed) {
-        const uint32_t at = atomicAdd(&C->ovf_listed, 1u);
-        if (at < OVF_LIST) ovf_list[at] = sl;
+        const uint32_t mine = atomicAdd(&my_ovf_n, 1u);
+        if (mine < OVF_BLOCK) {
+          my_ovf[mine] = sl;
+        } else {  // more than the block's list: the last block emits these
+          const uint32_t at = atomicAdd(&C->ovf_listed, 1u);
+          if (at < OVF_LIST) ovf_list[at] = sl;
+          ovf = true;
+        }
       }
       if (k[j] == EMPTY_KEY) side = true;
-      else ovf = true;
     }
 #endif
   }
@@ -2757,6 +2785,22 @@ __global__ void __launch_bounds__(THREADS, 2)
   if (side) atomicOr(&C->overflow_used[1], 1u);
   __syncthreads();
   sub_emit<ENT>(P, cc, 0);  // ends with a block barrier
+  {
+    const uint32_t m = my_ovf_n < OVF_BLOCK ? my_ovf_n : OVF_BLOCK;
+    if (m) {  // this block's overflow keys are complete: emit them
+      if (threadIdx.x == 0) {
+        my_ovf_base = atomicAdd(&C->out_count, (unsigned long long)m);
+        atomicAdd(&C->resident_groups[0], (unsigned long long)m);
+      }
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < m; i += THREADS) {
+        const uint32_t sl = my_ovf[i];
+        emit_one<ENT>(P, Ent<ENT>::at(P.ent, sl), my_ovf_base + i);
+        __stcg(reinterpret_cast<uint8_t*>(P.tags) + sl, (uint8_t)0);
+      }
+    }
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     last = atomicAdd(&C->done_count, 1u) == gridDim.x - 1;
