@@ -132,12 +132,18 @@ __device__ __forceinline__ long long sh_ld_volatile_s64(const long long* p) {
   return v;
 }
 
+#ifndef AGG_PASSC_PREFETCH
+#define AGG_PASSC_PREFETCH 1
+#endif
+#ifndef AGG_MINMAX_SKIP
+#define AGG_MINMAX_SKIP 1
+#endif
 __device__ __forceinline__ void sh_min_s64(long long* p, long long v) {
-  if (v < sh_ld_volatile_s64(p)) sh_red_min_s64(p, v);
+  if (!AGG_MINMAX_SKIP || v < sh_ld_volatile_s64(p)) sh_red_min_s64(p, v);
 }
 
 __device__ __forceinline__ void sh_max_s64(long long* p, long long v) {
-  if (v > sh_ld_volatile_s64(p)) sh_red_max_s64(p, v);
+  if (!AGG_MINMAX_SKIP || v > sh_ld_volatile_s64(p)) sh_red_max_s64(p, v);
 }
 
 __device__ __forceinline__ void smem_add_u64(unsigned long long* p, unsigned long long v) {
@@ -1292,7 +1298,7 @@ __device__ bool smem_round(const HashParams& P, const Team& T, Timer& tm, const 
       // claim the next sub-partition and stage its records in L2 while this one runs
       const uint32_t nx = atomicAdd(&C->sub_next[par], 1u);
       S.sub_q[(it + 1) & 1] = nx;
-      if (nx < nsub) {
+      if (AGG_PASSC_PREFETCH && nx < nsub) {
         const uint32_t a = __ldcg(&C->sub_base[par][nx]), b = __ldcg(&C->sub_base[par][nx + 1]);
         if (a < b && b <= tot) {
           for (uint32_t o = a; o < b; o += 4096)  // bulk prefetches of at most 64 KiB
