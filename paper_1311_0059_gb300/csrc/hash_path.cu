@@ -191,6 +191,9 @@ struct Smem {
   long long lead_mn, lead_mx;
   uint32_t lead_valid;
   uint32_t vote;
+  // the level at which run_groupby handed its records to the sort fallback
+  unsigned long long fb_nch;
+  uint32_t fb_level, fb_src, fb_dst, fb_set;
 };
 
 // Shared-memory table of partial states.  Counts are 32-bit (an entry is
@@ -1859,8 +1862,10 @@ __device__ __noinline__ bool fallback_sort(const HashParams& P, const Team& T, S
 // The whole group-by of one input by one team: level 0 over the input, then
 // the spilled levels.  Returns false when a bounded wait gave up (the team
 // must stop).
+constexpr int RUN_ABORT = 0, RUN_DONE = 1, RUN_FALLBACK = 2;
+
 template <int ENT, int VT>
-__device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const Cache& cc) {
+__device__ int run_groupby(const HashParams& P, const Team& T, Smem& S, const Cache& cc) {
   Ctrl* C = P.ctrl;
   const uint32_t fan = 1u << P.fan_log2;
   Timer tm, total;
@@ -1971,7 +1976,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     cache_flush<ENT>(P, cc, S);
     finalize_chunks(P, S, 0, 0);
     tm.lap(T, C, PH_L0);
-    if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+    if (!grid_barrier(T, C, P.timeout_ns, S)) return RUN_ABORT;
     tm.lap(T, C, PH_L0_WAIT);
     const unsigned long long spilled = ld_relaxed_u64(&C->pool_next[0]);
     emit_table<ENT>(P, T, cc, L.s_act, 0, S);
@@ -1979,9 +1984,9 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     if (spilled == 0) {
       total.lap(T, C, PH_TOTAL);
       final_step(P, T, 1);
-      return true;
+      return RUN_DONE;
     }
-    if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+    if (!grid_barrier(T, C, P.timeout_ns, S)) return RUN_ABORT;
     tm.lap(T, C, PH_ROUND_WAIT);
   }
 
@@ -1990,7 +1995,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
     if (level >= AGG_MAX_LEVELS) {
       if (threadIdx.x == 0 && T.bid == 0) set_status(C, AGG_ERR_INTERNAL);
       final_step(P, T, level);
-      return true;
+      return RUN_DONE;
     }
     const uint32_t src = (level + 1) & 1, dst = level & 1, set = level & 1;
     uint32_t* dpart = P.dir_part[src];
@@ -2047,35 +2052,19 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
       }
       S.cnt[p] = 0;
     }
-    if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+    if (!grid_barrier(T, C, P.timeout_ns, S)) return RUN_ABORT;
     if (ld_acquire_u32(&C->fallback_now)) {
-      // every record of this level: sorted by key, then reduced by segments
-      unsigned long long recs = 0;
-      for (uint32_t q = 0; q < fan; ++q) recs += __ldcg(&C->part_records[set][q]);
-      if (recs >= (1ull << 32)) {  // beyond the sort's 32-bit offsets
-        if (threadIdx.x == 0 && T.bid == 0) set_status(C, AGG_ERR_INTERNAL);
-        final_step(P, T, level + 1);
-        return true;
+      // every record of this level goes to the sort fallback (run by the
+      // caller, so that its calls stay out of this function's hot loops)
+      if (threadIdx.x == 0) {
+        S.fb_level = level;
+        S.fb_src = src;
+        S.fb_dst = dst;
+        S.fb_set = set;
+        S.fb_nch = nch;
       }
-      const uint32_t gsl = (P.slots / GTABLE_DIV) / BUCKET * BUCKET;
-      uint32_t* H = reinterpret_cast<uint32_t*>(P.ent + (size_t)gsl * Ent<ENT>::ES);
-      uint32_t* TOT = H + (size_t)T.nb * RADIX;
-      longlong2* bufA = reinterpret_cast<longlong2*>(P.stg[dst]);
-      longlong2* bufB = reinterpret_cast<longlong2*>(P.stg[src]);
-      if (!fallback_sort(P, T, S, cc, src, nch, recs, bufA, bufB, H, TOT)) return false;
-      const unsigned long long base = ld_relaxed_u64(&C->out_count);
-      unsigned long long ng = 0;
-      if (seg_reduce(P, T, S, RecordRows{bufB}, recs, false, base, &ng) < 0) return false;
-      if (threadIdx.x == 0 && T.bid == 0) {
-        C->out_count = base + ng;
-        C->resident_groups[level] += ng;
-        C->fallback_records = recs;
-        C->fallback_level = level;
-      }
-      restore_scratch<ENT>(P, T, gsl);
-      total.lap(T, C, PH_TOTAL);
-      final_step(P, T, level + 1);
-      return true;
+      __syncthreads();
+      return RUN_FALLBACK;
     }
     // P3: chunk lists grouped by partition
     if (threadIdx.x == 0) {
@@ -2093,7 +2082,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
       const uint32_t at = atomicAdd(&C->part_cursor[set][p], 1u);
       list[S.begin[p] + at] = (uint32_t)c;
     }
-    if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+    if (!grid_barrier(T, C, P.timeout_ns, S)) return RUN_ABORT;
     if (threadIdx.x == 0 && T.bid == 0) {
       for (uint32_t p = 0; p < MAX_FAN; ++p) {
         C->part_records[set ^ 1][p] = 0;
@@ -2142,7 +2131,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
         }
         if (!smem_round<ENT>(P, T, tm, G, S, cc, src, S.begin[p], S.begin[q], tot, rnd & 1, scratch, hrows,
                                  hstride))
-          return false;
+          return RUN_ABORT;
         if (threadIdx.x == 0 && T.bid == 0) C->rounds += 1;
         ++rnd;
         tm.lap(T, C, PH_ROUND_AGG);
@@ -2152,7 +2141,7 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
       // a partition too big for a shared-memory round: global-table round
       const uint32_t c0 = S.begin[p], c1 = S.begin[q];
       const uint64_t ntiles = c1 - c0;
-      if (!grid_barrier(T, C, P.timeout_ns, S)) return false;  // shared-memory rounds before it are complete
+      if (!grid_barrier(T, C, P.timeout_ns, S)) return RUN_ABORT;  // shared-memory rounds before it are complete
       for (uint64_t t = T.bid; t < ntiles; t += T.nb) {
         if (threadIdx.x == 0 && t + T.nb < ntiles && !P.stg_host) {  // one tile is one chunk (CH == TILE)
           const uint32_t nc = __ldcg(list + c0 + (uint32_t)(t + T.nb));
@@ -2174,17 +2163,17 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
       }
       cache_flush<ENT>(P, cc, S);
       tm.lap(T, C, PH_ROUND_AGG);
-      if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+      if (!grid_barrier(T, C, P.timeout_ns, S)) return RUN_ABORT;
       tm.lap(T, C, PH_ROUND_WAIT);
       emit_table<ENT>(P, T, cc, gslots, level, S);
       if (threadIdx.x == 0 && T.bid == 0) C->rounds += 1;
       tm.lap(T, C, PH_ROUND_EMIT);
-      if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+      if (!grid_barrier(T, C, P.timeout_ns, S)) return RUN_ABORT;
       tm.lap(T, C, PH_ROUND_WAIT);
       p = q;
     }
     finalize_chunks(P, S, dst, level);
-    if (!grid_barrier(T, C, P.timeout_ns, S)) return false;
+    if (!grid_barrier(T, C, P.timeout_ns, S)) return RUN_ABORT;
     tm.lap(T, C, PH_ROUND_WAIT);
     if (ld_acquire_u32(&C->overflow_used[level & 1])) emit_table<ENT>(P, T, cc, gslots, level, S);
     tm.lap(T, C, PH_ROUND_EMIT);
@@ -2192,13 +2181,49 @@ __device__ bool run_groupby(const HashParams& P, const Team& T, Smem& S, const C
       restore_scratch<ENT>(P, T, gslots);
       total.lap(T, C, PH_TOTAL);
       final_step(P, T, level + 1);
-      return true;
+      return RUN_DONE;
     }
   }
 }
 
+// The sort fallback of the level run_groupby stopped at (S.fb_*): sorts every
+// record of the level and reduces them by segments, then finishes the run.
+// False when a bounded wait gave up.
+template <int ENT>
+__device__ __noinline__ bool run_fallback(const HashParams& P, const Team& T, Smem& S, const Cache& cc) {
+  Ctrl* C = P.ctrl;
+  const uint32_t level = S.fb_level, src = S.fb_src, dst = S.fb_dst, set = S.fb_set;
+  const unsigned long long nch = S.fb_nch;
+  const uint32_t fan = 1u << P.fan_log2;
+  unsigned long long recs = 0;
+  for (uint32_t q = 0; q < fan; ++q) recs += __ldcg(&C->part_records[set][q]);
+  if (recs >= (1ull << 32)) {  // beyond the sort's 32-bit offsets
+    if (threadIdx.x == 0 && T.bid == 0) set_status(C, AGG_ERR_INTERNAL);
+    final_step(P, T, level + 1);
+    return true;
+  }
+  const uint32_t gsl = (P.slots / GTABLE_DIV) / BUCKET * BUCKET;
+  uint32_t* H = reinterpret_cast<uint32_t*>(P.ent + (size_t)gsl * Ent<ENT>::ES);
+  uint32_t* TOT = H + (size_t)T.nb * RADIX;
+  longlong2* bufA = reinterpret_cast<longlong2*>(P.stg[dst]);
+  longlong2* bufB = reinterpret_cast<longlong2*>(P.stg[src]);
+  if (!fallback_sort(P, T, S, cc, src, nch, recs, bufA, bufB, H, TOT)) return false;
+  const unsigned long long base = ld_relaxed_u64(&C->out_count);
+  unsigned long long ng = 0;
+  if (seg_reduce(P, T, S, RecordRows{bufB}, recs, false, base, &ng) < 0) return false;
+  if (threadIdx.x == 0 && T.bid == 0) {
+    C->out_count = base + ng;
+    C->resident_groups[level] += ng;
+    C->fallback_records = recs;
+    C->fallback_level = level;
+  }
+  restore_scratch<ENT>(P, T, gsl);
+  final_step(P, T, level + 1);
+  return true;
+}
+
 template <int ENT, int VT>
-__global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashParams P) {
+__global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const __grid_constant__ HashParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& S = *reinterpret_cast<Smem*>(smem_raw);
   const Cache cc = carve_cache(smem_raw + ((sizeof(Smem) + 15) & ~size_t(15)), P.ns, Ent<ENT>::MM);
@@ -2215,7 +2240,7 @@ __global__ void __launch_bounds__(THREADS, 2) hash_groupby_kernel(const HashPara
       return;
     }
   }
-  run_groupby<ENT, VT>(P, T, S, cc);
+  if (run_groupby<ENT, VT>(P, T, S, cc) == RUN_FALLBACK) run_fallback<ENT>(P, T, S, cc);
 }
 
 // Batched group-by: teams of `team_blocks` consecutive blocks; team t runs the
@@ -2234,7 +2259,9 @@ __global__ void __launch_bounds__(THREADS, 2)
   for (uint32_t j = team_off[team]; j < team_off[team + 1]; ++j) {
     const HashParams& P = items[team_items[j]];
     const Cache cc = carve_cache(smem_raw + ((sizeof(Smem) + 15) & ~size_t(15)), P.ns, Ent<ENT>::MM);
-    if (!run_groupby<ENT, VT>(P, T, S, cc)) return;
+    int r = run_groupby<ENT, VT>(P, T, S, cc);
+    if (r == RUN_FALLBACK) r = run_fallback<ENT>(P, T, S, cc) ? RUN_DONE : RUN_ABORT;
+    if (r == RUN_ABORT) return;
     if (!grid_barrier(T, P.ctrl, P.timeout_ns, S)) return;
   }
 }
