@@ -117,7 +117,16 @@ typedef struct agg_tuning {
                               0 = default (device memory; pinned host memory, which the kernel
                               reaches over the host link, when device memory cannot be had),
                               1 = device memory only, 2 = host memory.  Results do not depend on it */
+  uint32_t level0_slots;   /* slots of the level-0 table.  0 = default: at most AGG_LEVEL0_SLOTS.  A
+                              table whose entries run far past L2 makes every update of a group that
+                              is not hot a random read-modify-write in DRAM; with the cap the groups
+                              that fill it first stay resident (Pre-Partitioning, Section 4.3.4) and
+                              the rows of the others spill to level 1, whose rounds aggregate them in
+                              shared memory.  1 = the whole table the budget gives (the paper's
+                              sizing); else a cap of at least 4096 slots.  Results do not depend on it */
 } agg_tuning;
+
+#define AGG_LEVEL0_SLOTS 4194304u /* default cap of the level-0 table (2^22 slots) */
 
 /* Output arrays, device pointers owned by the caller, one row per group.
  * Arrays of aggregates not in spec.ops may be NULL; keys must not be NULL.

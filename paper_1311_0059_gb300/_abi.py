@@ -28,6 +28,7 @@ AGG_COUNT, AGG_SUM, AGG_MIN, AGG_MAX = 1, 2, 4, 8
 AGG_I32, AGG_I64 = 0, 1
 AGG_PATH_HASH, AGG_PATH_SORT, AGG_PATH_AUTO = 0, 1, 2
 AGG_MAX_LEVELS = 12
+AGG_LEVEL0_SLOTS = 1 << 22  # default cap of the level-0 table (slots)
 AGG_MIN_BUDGET = 1 << 20
 
 _P = ctypes.c_void_p
@@ -43,7 +44,8 @@ class agg_tuning(ctypes.Structure):
     _fields_ = [("max_load_factor", ctypes.c_double), ("smem_entries", ctypes.c_uint32),
                 ("fan_out", ctypes.c_uint32), ("warp_dedup", ctypes.c_uint32), ("wait_limit_us", ctypes.c_uint32),
                 ("fudge", ctypes.c_double), ("in_budget", ctypes.c_uint32), ("sorted_input", ctypes.c_uint32),
-                ("max_levels", ctypes.c_uint32), ("staging_tier", ctypes.c_uint32)]
+                ("max_levels", ctypes.c_uint32), ("staging_tier", ctypes.c_uint32),
+                ("level0_slots", ctypes.c_uint32)]
 
 
 class agg_output(ctypes.Structure):

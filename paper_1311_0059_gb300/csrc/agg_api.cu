@@ -109,7 +109,15 @@ agg_tuning effective(const agg_tuning* t) {
   e.sorted_input = (t && t->sorted_input) ? t->sorted_input : 1;
   e.max_levels = t ? t->max_levels : 0;
   e.staging_tier = t ? t->staging_tier : 0;
+  e.level0_slots = t ? t->level0_slots : 0;
   return e;
+}
+
+// Most slots the level-0 table may use (agg_tuning.level0_slots).
+uint64_t level0_cap(const agg_tuning& e) {
+  if (e.level0_slots == 0) return AGG_LEVEL0_SLOTS;
+  if (e.level0_slots == 1) return ~0ull;
+  return e.level0_slots;
 }
 
 bool valid_tuning(const agg_tuning* t) {
@@ -124,6 +132,7 @@ bool valid_tuning(const agg_tuning* t) {
   if (t->fudge < 0 || t->fudge > 16) return false;
   if (t->in_budget > 2 || t->sorted_input > 2 || t->staging_tier > 2) return false;
   if (t->max_levels >= AGG_MAX_LEVELS) return false;
+  if (t->level0_slots > 1 && t->level0_slots < MIN_SLOTS) return false;
   return true;
 }
 
@@ -175,10 +184,11 @@ bool layout_for(size_t budget, uint32_t es, Layout* L) {
   return s >= MIN_SLOTS && L->total <= budget;
 }
 
-uint32_t active_slots(uint64_t est, double lf, uint64_t slots) {
+uint32_t active_slots(uint64_t est, double lf, uint64_t slots, uint64_t cap = ~0ull) {
   uint64_t want = (uint64_t)((double)est / lf) + BUCKET;
   want = (want + BUCKET - 1) / BUCKET * BUCKET;
   if (want < MIN_SLOTS) want = MIN_SLOTS;
+  if (want > cap) want = cap / BUCKET * BUCKET;
   if (want > slots) want = slots;
   return (uint32_t)want;
 }
@@ -211,7 +221,8 @@ PathCosts path_costs(const agg_spec* s, const agg_tuning& t, uint64_t n, size_t 
   const double g = s->expected_groups ? std::min((double)s->expected_groups, rows) : rows;
   const double out = g * 8.0 * (1 + __builtin_popcount(s->ops & 15u));
   const double in = rows * (8.0 + vb);
-  const double k = t.max_load_factor * (double)slots;  // the table's planned groups (K)
+  // the level-0 table's planned groups (K)
+  const double k = t.max_load_factor * (double)std::min<uint64_t>(slots, level0_cap(t));
   if (n <= slots / 2) {
     c.hash_bytes = in + out;
     c.hash_s = c.hash_bytes / (INBUDGET_GBS * 1e9) + HASH_FIXED_S;
@@ -391,7 +402,7 @@ agg_status agg_plan(size_t budget, const agg_spec* spec, const agg_tuning* t, ui
   out->table_capacity = (uint64_t)(e.max_load_factor * (double)L.slots);
   out->fan_out = plan_fan(spec, e, n, budget, es);
   out->active_slots = active_slots(spec->expected_groups ? spec->expected_groups : (n ? n : 1),
-                                   e.max_load_factor, L.slots);
+                                   e.max_load_factor, L.slots, level0_cap(e));
   out->working_bytes = L.total;
   const uint64_t chunks = (n + CH - 1) / CH + 152ull * 2 * out->fan_out + 8;
   out->staging_bytes = 2 * (chunks * CH * REC_BYTES + 3 * chunks * 4);
@@ -633,7 +644,8 @@ agg_status hash_enqueue(agg_handle* h, const int64_t* d_keys, const void* d_vals
   p.ops = h->spec.ops;
   p.fan_log2 = log2u(fan);
   p.lf = h->tune.max_load_factor;
-  p.s_act0 = active_slots(h->spec.expected_groups ? h->spec.expected_groups : (n ? n : 1), p.lf, h->slots);
+  p.s_act0 = active_slots(h->spec.expected_groups ? h->spec.expected_groups : (n ? n : 1), p.lf, h->slots,
+                          level0_cap(h->tune));
   p.ns = h->tune.smem_entries > 1 ? h->tune.smem_entries : DEFAULT_NS;
   p.cache = h->tune.smem_entries != 1;
   p.dedup = h->tune.warp_dedup == 1 ? 1 : 0;
@@ -1026,7 +1038,7 @@ agg_status agg_batch_create(const agg_spec* spec, const agg_batch_item* items, u
     uint64_t need = (uint64_t)((double)(items[i].n ? items[i].n : 1) / tune.max_load_factor) + BUCKET;
     need = std::max<uint64_t>((need + BUCKET - 1) / BUCKET * BUCKET, 2 * MIN_SLOTS);
     plan[i].slots = std::min<uint64_t>(L.slots, need);  // never more than the input can use
-    plan[i].s_act0 = active_slots(est, tune.max_load_factor, plan[i].slots);
+    plan[i].s_act0 = active_slots(est, tune.max_load_factor, plan[i].slots, level0_cap(tune));
     plan[i].fan = plan_fan(&si, tune, items[i].n, items[i].budget, b->es);
     plan[i].may_spill = items[i].n > (uint64_t)(0.5 * (double)plan[i].slots);
   }
@@ -1451,7 +1463,8 @@ agg_status server_launch(agg_server* s, ServerQuery& sq, const QueryPlan& P, int
   p.ops = s->spec.ops;
   p.fan_log2 = log2u(P.fan);
   p.lf = s->tune.max_load_factor;
-  p.s_act0 = active_slots(q.expected_groups ? q.expected_groups : (n ? n : 1), p.lf, P.slots);
+  p.s_act0 = active_slots(q.expected_groups ? q.expected_groups : (n ? n : 1), p.lf, P.slots,
+                          level0_cap(s->tune));
   p.ns = s->tune.smem_entries;
   p.cache = 1;
   p.dedup = s->tune.warp_dedup == 1 ? 1 : 0;

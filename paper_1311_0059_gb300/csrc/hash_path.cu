@@ -191,6 +191,13 @@ struct Smem {
   long long lead_mn, lead_mx;
   uint32_t lead_valid;
   uint32_t vote;
+  // segmented scan: carry into each warp, head counts, warp-edge keys
+  unsigned long long wc_c[WARPS], wc_s[WARPS];
+  long long wc_mn[WARPS], wc_mx[WARPS];
+  uint32_t wc_f[WARPS];
+  uint32_t wh[WARPS + 1];
+  long long wl_key[WARPS], wf_key[WARPS];
+  long long tile_prev_key;
   // the level at which run_groupby handed its records to the sort fallback
   unsigned long long fb_nch;
   uint32_t fb_level, fb_src, fb_dst, fb_set;
@@ -1564,10 +1571,12 @@ __device__ __noinline__ int seg_reduce(const HashParams& P, const Team& T, Smem&
     if (threadIdx.x == 0 && t0 + TILE < r1)
       src.prefetch(t0 + TILE, r1 - t0 - TILE < (uint64_t)TILE ? r1 - t0 - TILE : TILE, false);
     const uint64_t row = t0 + 4ull * threadIdx.x;
+    long long k[4] = {0, 0, 0, 0}, v[4];
+    if (row < r1) src.load4(row, r1, k, v, false);
+    // the key before this thread's rows: the previous lane's last key, or a load
+    const long long up = __shfl_up_sync(FULL_MASK, k[3], 1);
     if (row >= r1) continue;
-    long long k[4], v[4];
-    src.load4(row, r1, k, v, false);
-    long long prev = row > 0 ? src.key(row - 1) : 0;
+    long long prev = lane > 0 ? up : (row > 0 ? src.key(row - 1) : 0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (row + j >= r1) break;
@@ -1608,6 +1617,7 @@ __device__ __noinline__ int seg_reduce(const HashParams& P, const Team& T, Smem&
     S.tc_mx = INT64_MIN;
     S.tc_f = 0;
     S.lead_valid = 0;
+    S.tile_prev_key = r0 > 0 && r0 < r1 ? src.key(r0 - 1) : 0;
   }
   __syncthreads();
   unsigned long long base = 0, n_groups = 0;
@@ -1624,10 +1634,19 @@ __device__ __noinline__ int seg_reduce(const HashParams& P, const Team& T, Smem&
       src.prefetch(t0 + TILE, r1 - t0 - TILE < (uint64_t)TILE ? r1 - t0 - TILE : TILE, true);
     const uint64_t row = t0 + 4ull * threadIdx.x;
     long long k[4] = {0, 0, 0, 0}, v[4] = {0, 0, 0, 0};
-    bool valid[4], head[4], last[4];
     if (row < r1) src.load4(row, r1, k, v, true);
-    const long long prev = row > 0 && row < r1 ? src.key(row - 1) : 0;
-    const long long next = row + 4 < n ? src.key(row + 4) : 0;
+    // neighbouring keys: shuffles inside a warp, shared memory across warps,
+    // one load past the tile
+    const long long up = __shfl_up_sync(FULL_MASK, k[3], 1);
+    const long long dn = __shfl_down_sync(FULL_MASK, k[0], 1);
+    if (lane == 31) S.wl_key[warp] = k[3];
+    if (lane == 0) S.wf_key[warp] = k[0];
+    long long edge_next = 0;
+    if (threadIdx.x == THREADS - 1 && row + 4 < n && row + 4 < r1) edge_next = src.key(row + 4);
+    __syncthreads();
+    const long long prev = lane > 0 ? up : (warp > 0 ? S.wl_key[warp - 1] : S.tile_prev_key);
+    const long long next = lane < 31 ? dn : (warp < WARPS - 1 ? S.wf_key[warp + 1] : edge_next);
+    bool valid[4], head[4], last[4];
     uint32_t my_heads = 0;
     Seg x = seg_identity();
 #pragma unroll
@@ -1639,14 +1658,17 @@ __device__ __noinline__ int seg_reduce(const HashParams& P, const Team& T, Smem&
       my_heads += head[j];
       if (valid[j]) x = seg_combine(x, Seg{1ull, (unsigned long long)v[j], v[j], v[j], head[j] ? 1u : 0u});
     }
-    uint32_t tile_total;
-    const uint32_t head_off = block_exclusive_scan(my_heads, tile_total, S);
-    // warp scan of the thread spans, then across warps
+    // warp scans of the spans and of the head counts
     Seg xi = x;
+    uint32_t hi = my_heads;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const Seg y = seg_shfl_up(xi, o);
-      if ((int)lane >= o) xi = seg_combine(y, xi);
+      const uint32_t hy = __shfl_up_sync(FULL_MASK, hi, o);
+      if ((int)lane >= o) {
+        xi = seg_combine(y, xi);
+        hi += hy;
+      }
     }
     Seg ex = seg_shfl_up(xi, 1);
     if (lane == 0) ex = seg_identity();
@@ -1656,13 +1678,50 @@ __device__ __noinline__ int seg_reduce(const HashParams& P, const Team& T, Smem&
       S.sw_mn[warp] = xi.mn;
       S.sw_mx[warp] = xi.mx;
       S.sw_f[warp] = xi.f;
+      S.wh[warp] = hi;
     }
     __syncthreads();
-    Seg carry{S.tc_c, S.tc_s, S.tc_mn, S.tc_mx, S.tc_f};
-    for (int w = 0; w < (int)warp; ++w)
-      carry = seg_combine(carry, Seg{S.sw_c[w], S.sw_s[w], S.sw_mn[w], S.sw_mx[w], S.sw_f[w]});
-    Seg acc = seg_combine(carry, ex);
-    unsigned long long hidx = base + tile_heads + head_off;  // heads up to and including the current row
+    if (warp == 0) {  // carry into each warp, and into the next tile
+      Seg t = lane < WARPS ? Seg{S.sw_c[lane], S.sw_s[lane], S.sw_mn[lane], S.sw_mx[lane], S.sw_f[lane]}
+                           : seg_identity();
+      uint32_t th = lane < WARPS ? S.wh[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const Seg y = seg_shfl_up(t, o);
+        const uint32_t hy = __shfl_up_sync(FULL_MASK, th, o);
+        if ((int)lane >= o) {
+          t = seg_combine(y, t);
+          th += hy;
+        }
+      }
+      const Seg carry{S.tc_c, S.tc_s, S.tc_mn, S.tc_mx, S.tc_f};
+      Seg wex = seg_shfl_up(t, 1);
+      const uint32_t hex = __shfl_up_sync(FULL_MASK, th, 1);
+      if (lane == 0) wex = seg_identity();
+      const Seg cin = seg_combine(carry, wex);
+      __syncwarp();
+      if (lane < WARPS) {
+        S.wc_c[lane] = cin.c;
+        S.wc_s[lane] = cin.s;
+        S.wc_mn[lane] = cin.mn;
+        S.wc_mx[lane] = cin.mx;
+        S.wc_f[lane] = cin.f;
+        S.wh[lane] = lane == 0 ? 0u : hex;
+      }
+      if (lane == WARPS - 1) {
+        const Seg nt = seg_combine(carry, t);
+        S.tc_c = nt.c;
+        S.tc_s = nt.s;
+        S.tc_mn = nt.mn;
+        S.tc_mx = nt.mx;
+        S.tc_f = nt.f;
+        S.wh[WARPS] = th;
+      }
+    }
+    __syncthreads();
+    Seg acc = seg_combine(Seg{S.wc_c[warp], S.wc_s[warp], S.wc_mn[warp], S.wc_mx[warp], S.wc_f[warp]}, ex);
+    unsigned long long hidx = base + tile_heads + S.wh[warp] + (hi - my_heads);  // heads before this thread's rows
+    const uint32_t tile_total = S.wh[WARPS];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (!valid[j]) break;
@@ -1688,16 +1747,7 @@ __device__ __noinline__ int seg_reduce(const HashParams& P, const Team& T, Smem&
         S.lead_valid = 1;
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {  // carry into the next tile: everything of this block so far
-      for (int w = 0; w < WARPS; ++w)
-        carry = seg_combine(carry, Seg{S.sw_c[w], S.sw_s[w], S.sw_mn[w], S.sw_mx[w], S.sw_f[w]});
-      S.tc_c = carry.c;
-      S.tc_s = carry.s;
-      S.tc_mn = carry.mn;
-      S.tc_mx = carry.mx;
-      S.tc_f = carry.f;
-    }
+    if (threadIdx.x == THREADS - 1) S.tile_prev_key = k[3];  // the key before the next tile
     tile_heads += tile_total;
     __syncthreads();
   }

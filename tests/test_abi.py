@@ -123,6 +123,25 @@ def test_depth_cap_knob_is_checked_on_the_host(lib):
         gb.plan(64 << 20, 10, spec, _abi.agg_tuning(staging_tier=3))
 
 
+def test_level0_table_cap(lib):
+    # the level-0 table takes at most AGG_LEVEL0_SLOTS slots unless asked for
+    # the whole budget (1) or another cap (>= 4096)
+    from paper_1311_0059_gb300 import groupby as gb, _abi
+    spec = gb.make_spec(ops=3, value_type=_abi.AGG_I64)
+    whole = gb.plan(1 << 30, 100_000_000, spec, _abi.agg_tuning(level0_slots=1))
+    assert whole["active_slots"] == whole["table_slots"] > _abi.AGG_LEVEL0_SLOTS
+    assert gb.plan(1 << 30, 100_000_000, spec)["active_slots"] == _abi.AGG_LEVEL0_SLOTS
+    assert gb.plan(1 << 30, 100_000_000, spec, _abi.agg_tuning(level0_slots=8192))["active_slots"] == 8192
+    assert gb.plan(1 << 30, 1000, spec)["active_slots"] < _abi.AGG_LEVEL0_SLOTS   # sized to n below the cap
+    # the cost model's resident capacity K follows the cap: more spill, more bytes
+    auto = gb.make_spec(ops=3, value_type=_abi.AGG_I64, path=_abi.AGG_PATH_AUTO, expected_groups=10_000_000)
+    capped = gb.plan(1 << 30, 100_000_000, auto)["hash_bytes"]
+    assert capped > gb.plan(1 << 30, 100_000_000, auto, _abi.agg_tuning(level0_slots=1))["hash_bytes"]
+    for bad in (2, 4095):
+        with pytest.raises(_abi.AggError):
+            gb.plan(64 << 20, 10, spec, _abi.agg_tuning(level0_slots=bad))
+
+
 def test_cost_model_chooses_between_the_paths(lib):
     # AGG_PATH_AUTO: the model in bytes (input, the Pre-Partitioning spill
     # R(1 - K/G) written and read, the level-1 sort when groups exceed 0.8 of

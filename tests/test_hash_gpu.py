@@ -135,13 +135,31 @@ def test_zipf_workload_scaled(oracle):
 
 @pytest.mark.parametrize("tune", [dict(), dict(max_load_factor=0.9), dict(smem_entries=1), dict(smem_entries=256),
                                   dict(warp_dedup=1), dict(warp_dedup=2), dict(fan_out=256),
-                                  dict(max_load_factor=0.2, fan_out=16)])
+                                  dict(max_load_factor=0.2, fan_out=16), dict(level0_slots=4096),
+                                  dict(level0_slots=1)])
 def test_result_invariant_under_tuning(oracle, tune):
     from paper_1311_0059_gb300 import agg_tuning
     w = dg.Workload("tune", n=1_500_000, domain=400_000, dist="zipf", zipf_s=0.8)
     keys, vals = w.host()
     got, _ = gpu_groupby(keys, vals, budget=2 * MB, tuning=agg_tuning(**tune))
     assert_parity(got, oracle_expected(oracle, keys, vals), what=str(tune))
+
+
+def test_level0_cap_spills_groups_the_whole_table_would_hold(oracle):
+    # 20k groups fit the 8 MB budget's table: uncapped, level 0 completes them
+    # all; capped at 4096 slots, the groups that fill the small table first
+    # stay resident and the rows of the others spill to level 1.  The result
+    # is the same.
+    from paper_1311_0059_gb300 import agg_tuning
+    keys, vals = rand_case(21, 400_000, 20_000)
+    exp = oracle_expected(oracle, keys, vals)
+    whole, st_w = gpu_groupby(keys, vals, budget=8 * MB, tuning=agg_tuning(level0_slots=1, sorted_input=2))
+    assert_parity(whole, exp, what="whole table")
+    assert st_w["spill_records"][0] == 0 and st_w["levels"] == 1
+    capped, st_c = gpu_groupby(keys, vals, budget=8 * MB, tuning=agg_tuning(level0_slots=4096, sorted_input=2))
+    assert_parity(capped, exp, what="level-0 table capped at 4096 slots")
+    assert st_c["spill_records"][0] > 0 and st_c["levels"] >= 2
+    assert st_c["resident_groups"][0] <= 4096
 
 
 @pytest.mark.parametrize("hint", [1, 1000, 400_000, 10**9])
