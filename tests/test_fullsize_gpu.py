@@ -78,8 +78,11 @@ def test_spilling_200m_rows_every_group():
 
 
 def test_skewed_500m_rows_every_group():
+    # the 10M groups would fit the 1 GB table, but the level-0 table stops at
+    # 2^22 slots: the groups that fill it first stay resident (the hot keys
+    # among them) and the tail's rows spill once
     st = _full_size(dg.ZIPF_500M_10M)
-    assert st["levels"] == 1
+    assert st["levels"] == 2 and st["spill_records"][0] > 0
 
 
 def test_plain_1m_rows_every_group():

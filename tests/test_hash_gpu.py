@@ -159,7 +159,7 @@ def test_level0_cap_spills_groups_the_whole_table_would_hold(oracle):
     capped, st_c = gpu_groupby(keys, vals, budget=8 * MB, tuning=agg_tuning(level0_slots=4096, sorted_input=2))
     assert_parity(capped, exp, what="level-0 table capped at 4096 slots")
     assert st_c["spill_records"][0] > 0 and st_c["levels"] >= 2
-    assert st_c["resident_groups"][0] <= 4096
+    assert st_c["resident_groups"][0] <= 4096 + 1  # the capped table, and the side slot of INT64_MIN
 
 
 @pytest.mark.parametrize("hint", [1, 1000, 400_000, 10**9])
@@ -264,7 +264,7 @@ def test_spill_200m_50m_full_size_sampled(oracle):
 
 def test_zipf_500m_10m_full_size_sampled(oracle):
     st = _sampled_full_size(oracle, dg.ZIPF_500M_10M)
-    assert st["levels"] == 1
+    assert st["levels"] == 2  # level-0 table capped at 2^22 slots: the tail spills once
 
 
 def _run_host_pinned(g, keys, vals, capacity):
