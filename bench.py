@@ -322,7 +322,7 @@ def measure_hash(w: dg.Workload, steps: int, warmup: int, world: int, local: int
     events on the launching stream; the roofline counts input, spill written,
     spill read and result bytes.  Returns the record and the live objects."""
     import torch
-    from paper_1311_0059_gb300 import AGG_I32, AGG_I64, AGG_PATH_HASH
+    from paper_1311_0059_gb300 import AGG_I32, AGG_I64, AGG_PATH_HASH, _abi
     from paper_1311_0059_gb300.costmodel import predicted_spill_records
     from paper_1311_0059_gb300.groupby import GroupBy, make_spec, plan
 
@@ -380,7 +380,9 @@ def measure_hash(w: dg.Workload, steps: int, warmup: int, world: int, local: int
            "fallback_records": stats["fallback_records"], "clocks": clocks.summary(),
            "l2": "inputs larger than L2, no flush" if copies == 1 else f"{copies} input copies rotated to defeat L2"}
     if spill_b:
-        k_cap = stats["table_capacity"]
+        # planned level-0 groups: the table's capacity, within the level-0 cap
+        k_cap = min(stats["table_capacity"],
+                    stats["table_capacity"] * _abi.AGG_LEVEL0_SLOTS // max(stats["table_slots"], 1))
         k_res = stats["resident_groups"][0]
         pred = predicted_spill_records(w.n, k_cap, n_groups)
         rec["spill"] = {"measured_records_level0": stats["spill_records"][0], "measured_bytes_total": spill_b,

@@ -29,6 +29,13 @@ constexpr uint32_t NSUB_MAX = 4096;        // sub-partitions of one shared-memor
 #define AGG_GTABLE_DIV 2
 #endif
 constexpr uint64_t ROUND_CAP_MAX = (uint64_t)AGG_ROUND_CAP_M << 20;  // records of one shared-memory round
+#ifndef AGG_ROUND_PACK_M
+#define AGG_ROUND_PACK_M 4
+#endif
+// Partitions are packed into one round only up to this many records: a round
+// this small stays in L2 from its count pass to its aggregate pass.  A single
+// partition up to ROUND_CAP_MAX still gets a round of its own.
+constexpr uint64_t ROUND_PACK_MAX = (uint64_t)AGG_ROUND_PACK_M << 20;
 // At recursion levels >= 1 the global table (keys that overflow a block's
 // shared-memory table, partitions too large for a shared-memory round) keeps
 // 1/GTABLE_DIV of the slots; the rest of the entry memory is round scratch.

@@ -2175,7 +2175,7 @@ __device__ int run_groupby(const HashParams& P, const Team& T, Smem& S, const Ca
       if (smem_ok && tot <= round_cap) {
         while (q < fan) {
           const uint64_t r = __ldcg(&C->part_records[set][q]);
-          if (tot + r > round_cap) break;
+          if (tot + r > round_cap || tot + r > ROUND_PACK_MAX) break;
           tot += r;
           ++q;
         }
